@@ -1,0 +1,199 @@
+/*
+ * CPU oracle for shortest-path distances -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load this
+ * library.  The product path (paper_1911_07260_gb300) never calls it and shares no
+ * code, header, table or helper with it.
+ *
+ * What it computes.  Delta-stepping with or without bucket fusion (Section 3, the
+ * lazy / eager / eager-with-fusion figures) is a label-correcting method that stops only
+ * when no bucket holds a vertex whose distance can still improve, so it reaches exactly
+ * the shortest-path distances of the plain definition (Section 6.1, "SSSP and wBFS"):
+ *     dist(v) = min over paths s -> v of the sum of edge weights, or "unreachable".
+ * The oracle computes that definition directly:
+ *   - or_dijkstra:      binary-heap Dijkstra with lazy deletion, 64-bit sums.  With a
+ *                       target it stops once the target is popped (its value is final),
+ *                       which is the PPSP / A* result (Section 6.1, "PPSP", "A* Search").
+ *   - or_bfs:           hop counts (unit weights), the wBFS special case.
+ *   - or_bellman_ford:  repeated relaxation of every edge until nothing changes; the
+ *                       unordered method of Section 1, used as an independent check.
+ *   - or_check_sssp:    certificate check: dist[src] = 0; for every edge u->v with u
+ *                       reached, dist[v] <= dist[u] + w; every reached v != src has an
+ *                       in-edge with equality; unreached vertices hold the sentinel.
+ *                       With every weight >= 1 these conditions imply exactness.
+ *
+ * Conventions.  Distances are uint32 with 0xFFFFFFFF = unreachable (the paper's INT_MAX
+ * initialisation, Section 4.1).  A finite distance >= 0xFFFFFFFE cannot be represented;
+ * the oracle then returns OR_OVERFLOW and stores 0xFFFFFFFE.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_OVERFLOW 1
+#define OR_INVALID (-1)
+#define OR_NOMEM (-2)
+
+#define UNREACHED 0xFFFFFFFFu
+#define SATURATED 0xFFFFFFFEu
+#define NO_TARGET 0xFFFFFFFFu
+
+typedef struct {
+  uint64_t key;
+  uint32_t v;
+} heap_item;
+
+/* Plain binary min-heap on key. */
+static void heap_push(heap_item *h, uint64_t *size, heap_item x) {
+  uint64_t i = (*size)++;
+  while (i > 0) {
+    uint64_t p = (i - 1) / 2;
+    if (h[p].key <= x.key) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i] = x;
+}
+
+static heap_item heap_pop(heap_item *h, uint64_t *size) {
+  heap_item top = h[0];
+  heap_item last = h[--(*size)];
+  uint64_t i = 0, n = *size;
+  for (;;) {
+    uint64_t l = 2 * i + 1, r = l + 1, s = i;
+    uint64_t best_key = last.key;
+    if (l < n && h[l].key < best_key) { s = l; best_key = h[l].key; }
+    if (r < n && h[r].key < best_key) { s = r; }
+    if (s == i) break;
+    h[i] = h[s];
+    i = s;
+  }
+  if (n > 0) h[i] = last;
+  return top;
+}
+
+static int store_dist(uint32_t n, const uint64_t *d64, uint32_t *dist_out) {
+  int st = OR_OK;
+  for (uint32_t v = 0; v < n; ++v) {
+    if (d64[v] == UINT64_MAX) dist_out[v] = UNREACHED;
+    else if (d64[v] >= SATURATED) { dist_out[v] = SATURATED; st = OR_OVERFLOW; }
+    else dist_out[v] = (uint32_t)d64[v];
+  }
+  return st;
+}
+
+/* Dijkstra from src.  target == 0xFFFFFFFF: all distances.  Otherwise stops when the
+ * target is popped; dist_out[target] is then final (other entries are upper bounds). */
+int or_dijkstra(uint32_t n, const uint64_t *off, const uint32_t *nbr, const uint32_t *w,
+                uint32_t src, uint32_t target, uint32_t *dist_out) {
+  if (n == 0 || src >= n || (target != NO_TARGET && target >= n)) return OR_INVALID;
+  uint64_t m = off[n];
+  uint64_t *d = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  heap_item *h = (heap_item *)malloc(sizeof(heap_item) * (m + 1));
+  unsigned char *done = (unsigned char *)calloc(n, 1);
+  if (!d || !h || !done) { free(d); free(h); free(done); return OR_NOMEM; }
+  for (uint32_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
+  uint64_t hs = 0;
+  d[src] = 0;
+  heap_item s0 = {0, src};
+  heap_push(h, &hs, s0);
+  while (hs > 0) {
+    heap_item it = heap_pop(h, &hs);
+    uint32_t u = it.v;
+    if (done[u] || it.key != d[u]) continue; /* lazy deletion of stale heap entries */
+    done[u] = 1;
+    if (u == target) break;
+    for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = nbr[e];
+      uint64_t nd = d[u] + w[e];
+      if (nd < d[v]) {
+        d[v] = nd;
+        heap_item x = {nd, v};
+        heap_push(h, &hs, x);
+      }
+    }
+  }
+  int st = store_dist(n, d, dist_out);
+  free(d); free(h); free(done);
+  return st;
+}
+
+/* Breadth-first hop counts from src (every edge counts 1). */
+int or_bfs(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t src,
+           uint32_t *dist_out) {
+  if (n == 0 || src >= n) return OR_INVALID;
+  uint32_t *q = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  if (!q) return OR_NOMEM;
+  for (uint32_t v = 0; v < n; ++v) dist_out[v] = UNREACHED;
+  uint64_t head = 0, tail = 0;
+  dist_out[src] = 0;
+  q[tail++] = src;
+  while (head < tail) {
+    uint32_t u = q[head++];
+    for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = nbr[e];
+      if (dist_out[v] == UNREACHED) {
+        dist_out[v] = dist_out[u] + 1;
+        q[tail++] = v;
+      }
+    }
+  }
+  free(q);
+  return OR_OK;
+}
+
+/* Bellman-Ford: relax every edge, repeat until a full pass changes nothing (at most
+ * n passes with non-negative weights). */
+int or_bellman_ford(uint32_t n, const uint64_t *off, const uint32_t *nbr,
+                    const uint32_t *w, uint32_t src, uint32_t *dist_out) {
+  if (n == 0 || src >= n) return OR_INVALID;
+  uint64_t *d = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  if (!d) return OR_NOMEM;
+  for (uint32_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
+  d[src] = 0;
+  for (uint32_t pass = 0; pass < n; ++pass) {
+    int changed = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+      if (d[u] == UINT64_MAX) continue;
+      for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+        uint64_t nd = d[u] + w[e];
+        if (nd < d[nbr[e]]) { d[nbr[e]] = nd; changed = 1; }
+      }
+    }
+    if (!changed) break;
+  }
+  int st = store_dist(n, d, dist_out);
+  free(d);
+  return st;
+}
+
+/* Certificate check of an SSSP result.  Returns 0 if valid, else a code and the first
+ * offending vertex in *bad:
+ *   1: dist[src] != 0            2: an edge u->v with dist[v] > dist[u] + w
+ *   3: reached v != src without a tight in-edge
+ *   4: a value equal to the saturation marker 0xFFFFFFFE                              */
+int or_check_sssp(uint32_t n, const uint64_t *off, const uint32_t *nbr, const uint32_t *w,
+                  uint32_t src, const uint32_t *dist, uint32_t *bad) {
+  if (n == 0 || src >= n) return OR_INVALID;
+  *bad = 0;
+  if (dist[src] != 0) { *bad = src; return 1; }
+  unsigned char *tight = (unsigned char *)calloc(n, 1);
+  if (!tight) return OR_NOMEM;
+  int code = 0;
+  for (uint32_t u = 0; u < n && !code; ++u) {
+    if (dist[u] == SATURATED) { *bad = u; code = 4; break; }
+    if (dist[u] == UNREACHED) continue;
+    for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t v = nbr[e];
+      uint64_t cand = (uint64_t)dist[u] + w[e];
+      uint64_t dv = dist[v] == UNREACHED ? UINT64_MAX : dist[v];
+      if (dv > cand) { *bad = v; code = 2; break; }
+      if (dv == cand) tight[v] = 1;
+    }
+  }
+  for (uint32_t v = 0; v < n && !code; ++v)
+    if (v != src && dist[v] != UNREACHED && !tight[v]) { *bad = v; code = 3; }
+  free(tight);
+  return code;
+}

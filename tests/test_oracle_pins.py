@@ -1,0 +1,196 @@
+"""Pins for the CPU oracle against things other than itself (CPU only).
+
+* hand-worked fixtures (tests/golden/hand_worked.txt),
+* brute-force enumeration of simple paths on tiny graphs,
+* scipy.sparse.csgraph's Dijkstra (an independent library routine),
+* closed forms: path prefix sums, constant-weight grids (c * Manhattan distance),
+  unit weights (BFS hop counts), stars, disconnected parts,
+* the certificate (edge) invariant and its sensitivity to planted mistakes.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from tests.golden import fixtures
+
+INF = 0xFFFFFFFF
+
+
+def _brute(n, edges, src):
+    """Minimum over all simple paths from src (exhaustive DFS; tiny n only)."""
+    adj = [[] for _ in range(n)]
+    for u, v, w in edges:
+        adj[u].append((v, w))
+    best = [None] * n
+
+    def dfs(u, acc, seen):
+        if best[u] is None or acc < best[u]:
+            best[u] = acc
+        for v, w in adj[u]:
+            if v not in seen:
+                seen.add(v)
+                dfs(v, acc + w, seen)
+                seen.remove(v)
+
+    dfs(src, 0, {src})
+    return [INF if b is None else b for b in best]
+
+
+def _edges_of(g):
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets).astype(np.int64))
+    return list(zip(src.tolist(), g.nbr.tolist(), g.w.tolist()))
+
+
+def test_golden_fixtures(gg, orc):
+    cases = fixtures.load()
+    assert len(cases) >= 5
+    for c in cases:
+        s, d, w = zip(*c["edges"])
+        g = gg.from_edges(c["n"], s, d, w)
+        if c["target"] is None:
+            assert orc.dijkstra(g, c["src"]).tolist() == c["expect"], c["name"]
+            assert orc.bellman_ford(g, c["src"]).tolist() == c["expect"], c["name"]
+        else:
+            assert orc.ppsp(g, c["src"], c["target"]) == c["expect"][0], c["name"]
+
+
+@pytest.mark.parametrize("seed", range(300))
+def test_dijkstra_vs_brute_force(gg, orc, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 7))
+    m = int(rng.integers(0, 14))
+    g = gg.random_graph(n, m, wlo=0, whi=int(rng.choice([2, 5, 50])), seed=seed)
+    src = int(rng.integers(0, n))
+    ref = _brute(n, _edges_of(g), src)
+    assert orc.dijkstra(g, src).tolist() == ref
+    assert orc.bellman_ford(g, src).tolist() == ref
+    for t in range(n):
+        assert orc.ppsp(g, src, t) == ref[t]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_dijkstra_vs_scipy(gg, orc, seed):
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(20, 300))
+    m = int(rng.integers(n, 6 * n))
+    g = gg.random_graph(n, m, wlo=1, whi=int(rng.choice([3, 100, 100000])), seed=seed,
+                       symmetric=bool(seed % 2), self_loops=True)
+    # scipy sums duplicate entries, so collapse parallel edges to their minimum first;
+    # self loops never shorten a path and are dropped.
+    best = {}
+    for u, v, w in _edges_of(g):
+        if u != v:
+            best[(u, v)] = min(w, best.get((u, v), w))
+    if best:
+        rows, cols = zip(*best.keys())
+        vals = list(best.values())
+    else:
+        rows, cols, vals = [], [], []
+    mat = sp.csr_matrix((np.array(vals, float), (rows, cols)), shape=(n, n))
+    for src in rng.integers(0, n, 3):
+        ref = csg.dijkstra(mat, directed=True, indices=int(src))
+        ref = np.where(np.isinf(ref), INF, ref).astype(np.uint64)
+        got = orc.dijkstra(g, int(src))
+        np.testing.assert_array_equal(got.astype(np.uint64), ref)
+
+
+def test_path_prefix_sums(gg, orc):
+    w = np.array([5, 0, 17, 1, 999, 3, 0, 42], np.uint32)
+    g = gg.path_graph(w)
+    expect = np.concatenate([[0], np.cumsum(w)])
+    np.testing.assert_array_equal(orc.dijkstra(g, 0), expect)
+    # Everything before the source is unreachable on a directed path.
+    d = orc.dijkstra(g, 3)
+    assert (d[:3] == INF).all()
+    np.testing.assert_array_equal(d[3:], np.concatenate([[0], np.cumsum(w[3:])]))
+
+
+@pytest.mark.parametrize("c", [1, 7, 1000])
+def test_constant_grid_is_manhattan(gg, orc, c):
+    k = 23
+    g = gg.grid(k, k, c, c + 1, seed=3)
+    assert (g.w == c).all()
+    for src in [0, k * k - 1, 5 * k + 11]:
+        r0, c0 = divmod(src, k)
+        rr, cc = np.divmod(np.arange(k * k), k)
+        manhattan = (np.abs(rr - r0) + np.abs(cc - c0)) * c
+        np.testing.assert_array_equal(orc.dijkstra(g, src), manhattan)
+        np.testing.assert_array_equal(orc.bfs(g, src) * c, manhattan)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_unit_weights_equal_bfs(gg, orc, seed):
+    g = gg.random_graph(200, 700, wlo=1, whi=2, seed=seed, symmetric=bool(seed % 2))
+    for src in (0, 17, 199):
+        np.testing.assert_array_equal(orc.dijkstra(g, src), orc.bfs(g, src))
+
+
+def test_star_and_disconnected(gg, orc):
+    # star 0 -> 1..9 with weight i, plus an isolated component {10, 11}.
+    s = [0] * 9 + [10]
+    d = list(range(1, 10)) + [11]
+    w = list(range(1, 10)) + [4]
+    g = gg.from_edges(12, s, d, w)
+    got = orc.dijkstra(g, 0)
+    assert got.tolist() == [0] + list(range(1, 10)) + [INF, INF]
+    assert orc.dijkstra(g, 10).tolist() == [INF] * 10 + [0, 4]
+
+
+def test_overflow_is_reported(gg, orc):
+    g = gg.path_graph([0xFFFFFFF0, 0x10, 0x10])
+    with pytest.raises(orc.OracleError):
+        orc.dijkstra(g, 0)
+    d = orc.dijkstra(g, 0, allow_overflow=True)
+    assert d[1] == 0xFFFFFFF0 and d[2] == orc.SATURATED and d[3] == orc.SATURATED
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_certificate_accepts_oracle_and_rejects_planted_mistakes(gg, orc, seed):
+    g = gg.random_graph(300, 1500, wlo=1, whi=50, seed=seed, symmetric=True)
+    src = seed
+    d = orc.dijkstra(g, src)
+    assert orc.check_sssp(g, src, d) == (0, 0)
+    reached = np.nonzero((d != INF) & (np.arange(g.n) != src))[0]
+    assert reached.size > 10
+    v = int(reached[seed % reached.size])
+    up = d.copy(); up[v] += 1          # too large: some in-edge is violated
+    assert orc.check_sssp(g, src, up)[0] == 2
+    down = d.copy(); down[v] -= 1      # too small: no tight in-edge
+    assert orc.check_sssp(g, src, down)[0] in (2, 3)
+    lost = d.copy(); lost[v] = INF     # dropped vertex
+    assert orc.check_sssp(g, src, lost)[0] == 2
+    bad_src = d.copy(); bad_src[src] = 1
+    assert orc.check_sssp(g, src, bad_src)[0] == 1
+
+
+def test_pins_catch_plausible_oracle_mistakes(gg, orc):
+    """Run the oracle on mutated inputs that model a transposed operand (edges read
+    backwards) and a misindexed weight array; the brute-force pin must reject both."""
+    rejected_t = rejected_w = 0
+    for seed in range(40):
+        g = gg.random_graph(6, 10, wlo=1, whi=20, seed=seed, self_loops=False)
+        e = _edges_of(g)
+        ref = _brute(g.n, e, 0)
+        rev = gg.from_edges(g.n, [x[1] for x in e], [x[0] for x in e], [x[2] for x in e])
+        rejected_t += orc.dijkstra(rev, 0).tolist() != ref
+        shifted = gg.Graph("shift", g.offsets, g.nbr, np.roll(g.w, 1))
+        rejected_w += orc.dijkstra(shifted, 0).tolist() != ref
+    assert rejected_t > 20 and rejected_w > 20
+
+
+def test_ppsp_stops_at_target_with_final_value(gg, orc):
+    g = gg.grid(40, 40, 1, 1000, seed=5)
+    full = orc.dijkstra(g, 0)
+    for t in [1, 39, 800, 1599]:
+        assert orc.ppsp(g, 0, t) == int(full[t])
+
+
+def test_oracle_rejects_bad_arguments(gg, orc):
+    g = gg.path_graph([1, 2])
+    with pytest.raises(orc.OracleError):
+        orc.dijkstra(g, 3)
+    with pytest.raises(orc.OracleError):
+        orc.dijkstra(g, 0, target=9)
