@@ -1,0 +1,203 @@
+/*
+ * og.h -- C ABI of the GB300 ordered shortest-path library (libog.so).
+ *
+ * The library computes single-source and point-to-point shortest paths with
+ * Delta-stepping over a bucketed priority queue, using eager bucket updates and bucket
+ * fusion (Section 3.2, "Eager Bucket Update", and Section 3.3, "Eager Bucket Fusion
+ * Optimization", with the figure "SSSP with the eager bucket update approach and the
+ * bucket fusion optimization").  Weighted BFS, PPSP and A* are variants of the same
+ * loop (Section 6.1, "Applications").  Every step runs in CUDA kernels for sm_103a; there
+ * is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Vertices are uint32 ids in [0, n).  Weights are non-negative uint32.
+ *   - Distances are uint32; 0xFFFFFFFF means "unreachable" (the INT_MAX initialisation
+ *     of the paper's priority vector, Section 4.1).  A path whose length reaches
+ *     0xFFFFFFFE saturates there and the call returns OG_E_OVERFLOW.
+ *   - "stream" is a cudaStream_t (NULL = legacy default stream).  Work is issued on it.
+ *     Single-query calls and og_batch_run synchronise that stream before returning so
+ *     they can report a status; device outputs are complete when they return OG_OK.
+ *   - Ownership: the caller owns every buffer it passes; the library owns the og_graph
+ *     and its device copies and scratch (bucket arenas, query state), and frees them in
+ *     og_graph_free / og_server_free.
+ *   - Errors: every int-returning call returns OG_OK (0) or one of the OG_E_* codes.  On
+ *     error the outputs are unspecified.  No call aborts the process.
+ *   - Thread safety: calls on one og_graph (or one og_server) must not overlap.
+ */
+#ifndef OG_H
+#define OG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OG_OK 0
+#define OG_E_INVALID 1   /* bad argument: n = 0, vertex out of range, offsets not
+                            monotone, m >= 2^32, zero weight on wBFS, ...            */
+#define OG_E_OOM 2       /* device or host allocation failed                         */
+#define OG_E_CUDA 3      /* a CUDA runtime call failed (og_last_cuda_error tells which) */
+#define OG_E_OVERFLOW 4  /* a distance reached the saturation value 0xFFFFFFFE       */
+#define OG_E_TIMEOUT 5   /* a bounded device wait (grid barrier) gave up             */
+#define OG_E_BUSY 6      /* no free serving slot                                      */
+#define OG_E_ARENA 7     /* bucket arena exhausted even after regrowth                */
+
+/* Query kinds (Section 6.1). */
+#define OG_Q_SSSP 0      /* all distances from src                                    */
+#define OG_Q_PPSP 1      /* dist(src, dst); stops on entering bucket i with
+                            i * Delta >= best dist(src, dst) found so far             */
+#define OG_Q_ASTAR 2     /* dist(src, dst) with priority g + h, h = floor(100 * Euclid) */
+#define OG_Q_WBFS 3      /* SSSP with Delta = 1 (positive integer weights required)   */
+
+typedef struct og_graph og_graph;
+typedef struct og_server og_server;
+
+/* Schedule knobs: the scheduling language of Section 4.2 (Table "Scheduling functions
+ * for applyUpdatePriority operators") as plain fields.  0 selects the graph's tuned or
+ * default value for every field. */
+typedef struct og_config {
+  uint32_t delta;            /* priority coarsening factor (Section 2), >= 1          */
+  uint32_t fusion_threshold; /* bucket fusion: a CTA keeps draining its local bin of the
+                                current bucket while 0 < size < threshold (Section 3.3);
+                                OG_FUSION_OFF disables fusion, 0xFFFFFFFF = unbounded   */
+  uint32_t expand_tile;      /* frontier entries a CTA claims per grab (multiple of 32) */
+  uint32_t blocks_per_sm;    /* persistent CTAs per SM (capped by occupancy)           */
+  uint32_t ring_buckets;     /* materialised buckets (power of two, <= 64); further
+                                buckets go to one overflow pile (Section 5.1's lazy
+                                queue idea of a few materialised buckets + overflow)   */
+  uint32_t reserved0;
+  uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
+  uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
+} og_config;
+
+#define OG_FUSION_OFF 0xFFFFFFFEu
+
+/* Counters of one call (summed over its queries). */
+typedef struct og_stats {
+  uint64_t rounds;           /* global rounds (grid-wide barriers between phases)      */
+  uint64_t fused_iters;      /* CTA-local fused iterations (summed over CTAs)          */
+  uint64_t items;            /* bucket entries dequeued                                */
+  uint64_t stale;            /* dequeued entries skipped as out of date                */
+  uint64_t relax;            /* edges relaxed                                          */
+  uint64_t improved;         /* relaxations that lowered a distance                    */
+  uint64_t local_inserts;    /* inserts kept in a CTA-local bin (fusion)               */
+  uint64_t global_inserts;   /* inserts into materialised global buckets               */
+  uint64_t overflow_inserts; /* inserts into the overflow pile                         */
+  uint64_t redistributions;  /* overflow-pile redistributions                          */
+  uint64_t restarts;         /* arena regrowth restarts                                */
+  uint64_t kernel_ns;        /* device time of the persistent kernel(s), CUDA events   */
+  uint64_t reserved[4];
+} og_stats;
+
+typedef struct og_query {
+  uint32_t kind;             /* OG_Q_*                                                 */
+  uint32_t src;
+  uint32_t dst;              /* PPSP / A*: target; ignored otherwise                   */
+  uint32_t delta;            /* 0 = config / graph default                             */
+} og_query;
+
+/* ---- graph -------------------------------------------------------------------------
+ * og_graph_upload: copies a CSR graph to the device (Section 4.1: an edgeset with
+ * integer weights).  offsets: host uint64[n+1], non-decreasing, offsets[0] = 0,
+ * offsets[n] = m < 2^32.  neighbors, weights: host uint32[m]; the out-edges of u are
+ * neighbors[offsets[u] .. offsets[u+1]) with the matching weights.  The library keeps
+ * its own copy (uint32 offsets, interleaved {neighbor, weight} pairs).  Returns
+ * OG_E_INVALID for n = 0, bad offsets or a neighbor >= n. */
+int og_graph_upload(const uint64_t* offsets, const uint32_t* neighbors,
+                    const uint32_t* weights, uint32_t n, uint64_t m, void* stream,
+                    og_graph** out);
+
+/* Vertex coordinates for A*: float32[2n] as (x, y) pairs, host or device pointer (the
+ * library detects which).  Copied.  The A* heuristic is floor(100 * Euclidean distance)
+ * to the target; with integral coordinates below 2^24 it is computed exactly in
+ * integers, otherwise as max(0, floor(100 * d) - 1) in double. */
+int og_graph_set_coords(og_graph* g, const float* xy, void* stream);
+
+/* n, m, minimum and maximum edge weight (any pointer may be NULL). */
+int og_graph_info(const og_graph* g, uint32_t* n, uint64_t* m, uint32_t* min_w,
+                  uint32_t* max_w);
+
+/* Graph-level default schedule (og_autotune writes one).  0 fields keep defaults. */
+int og_graph_set_config(og_graph* g, const og_config* cfg);
+int og_graph_get_config(const og_graph* g, og_config* cfg);
+
+void og_graph_free(og_graph* g);
+
+/* Library defaults (Delta 0 = derived from the weights, fusion 1024, ...). */
+void og_config_default(og_config* cfg);
+
+/* ---- single queries -----------------------------------------------------------------
+ * og_sssp_delta: Delta-stepping SSSP from src with eager bucket update and bucket
+ * fusion (Section 3.3).  delta 0 = graph default.  dist_out: uint32[n], host or device
+ * pointer; on OG_OK it holds every distance from src. */
+int og_sssp_delta(og_graph* g, uint32_t src, uint32_t delta, uint32_t* dist_out,
+                  void* stream);
+
+/* og_wbfs: weighted BFS = SSSP with Delta = 1 (Section 6.1, "SSSP and wBFS"); every
+ * weight must be >= 1 (OG_E_INVALID otherwise). */
+int og_wbfs(og_graph* g, uint32_t src, uint32_t* dist_out, void* stream);
+
+/* og_ppsp: point-to-point distance (Section 6.1, "PPSP"): Delta-stepping from src that
+ * stops on entering bucket i with i * Delta >= the best dist(src, dst) found.
+ * d_out: host uint32, receives dist(src, dst) (0xFFFFFFFF if unreachable). */
+int og_ppsp(og_graph* g, uint32_t src, uint32_t dst, uint32_t delta, uint32_t* d_out,
+            void* stream);
+
+/* og_astar: A* (Section 6.1, "A* Search"): the bucket of a vertex is
+ * floor((g + h) / Delta) with h = floor(100 * Euclidean distance to dst) from the
+ * coordinates.  coords: float32[2n] (host or device) or NULL to use
+ * og_graph_set_coords.  Same stop rule and output as og_ppsp.  If the heuristic proves
+ * inconsistent on some edge the query keeps running until its buckets are empty, so the
+ * result stays exact. */
+int og_astar(og_graph* g, uint32_t src, uint32_t dst, const float* coords,
+             uint32_t delta, uint32_t* d_out, void* stream);
+
+/* Any query kind with an explicit schedule and counters (cfg and stats may be NULL).
+ * dist_out (SSSP / wBFS: uint32[n], host or device; PPSP / A*: may be NULL) and d_out
+ * (host uint32; PPSP / A*: dist(src, dst); may be NULL). */
+int og_query_run(og_graph* g, const og_query* q, const og_config* cfg,
+                 uint32_t* dist_out, uint32_t* d_out, og_stats* stats, void* stream);
+
+/* ---- batches (many queries, one persistent launch) ------------------------------------
+ * Runs nq queries concurrently: each has its own distance array and bucket ring, all
+ * share one persistent kernel and its rounds.  q: host array of nq queries.
+ * dist_out: uint32[nq * n] (host or device; query i at dist_out + i*n) or NULL when
+ * only d_out is wanted.  d_out: host uint32[nq] (dist(src, dst) for PPSP / A*, 0 for
+ * the others) or NULL. */
+int og_batch_run(og_graph* g, const og_query* q, uint32_t nq, const og_config* cfg,
+                 uint32_t* dist_out, uint32_t* d_out, og_stats* stats, void* stream);
+
+/* ---- serving (continuous batching) -----------------------------------------------------
+ * A server keeps the graph and up to max_slots queries resident.  og_server_submit
+ * admits a PPSP / A* / SSSP query into a free slot (OG_E_BUSY if none).  og_server_step
+ * advances every admitted query by up to max_rounds rounds in one persistent launch;
+ * queries admitted between steps join the next launch.  og_server_poll returns finished
+ * queries (tag and dist(src, dst)) and frees their slots.  Results do not depend on what
+ * else is in flight.  max_slots = 0 sizes the slot count from free device memory. */
+int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void* stream,
+                     og_server** out);
+int og_server_submit(og_server* s, const og_query* q, uint64_t tag);
+int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active);
+int og_server_poll(og_server* s, uint64_t* tags, uint32_t* d_out, uint32_t cap,
+                   uint32_t* n_done);
+int og_server_slots(const og_server* s, uint32_t* max_slots, uint32_t* n_free);
+void og_server_free(og_server* s);
+
+/* ---- autotuning (Section 5.3) ------------------------------------------------------------
+ * Times the given sample queries under candidate schedules (Delta over powers of two in
+ * [delta_lo, delta_hi], then the fusion threshold, then the expansion tile) and returns
+ * the fastest in *out (also stored as the graph default).  kind: OG_Q_*.  srcs / dsts:
+ * host arrays of nsample sources (and targets for PPSP / A*; NULL otherwise). */
+int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t* dsts,
+                uint32_t nsample, uint32_t delta_lo, uint32_t delta_hi, og_config* out);
+
+/* ---- diagnostics ----------------------------------------------------------------------- */
+const char* og_strerror(int code);
+const char* og_last_cuda_error(void);
+int og_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OG_H */

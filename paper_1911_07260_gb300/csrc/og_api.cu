@@ -1,0 +1,897 @@
+// Host side of libog: the C ABI declared in include/og.h.
+//
+// Every call validates its arguments on the host, stages query descriptors through
+// pinned memory, and runs the Delta-stepping kernels of og_kernels.cu on the caller's
+// stream.  Scratch (bucket rings, overflow piles, query cursors) is owned by the graph
+// (single queries, batches) or by a server, grown on demand and reused across calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "og.h"
+#include "og_internal.cuh"
+
+namespace og {
+cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st);
+cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t launch_fill(uint32_t* dist, uint32_t n, const uint32_t* slots, uint32_t nslots,
+                        int sms, cudaStream_t st);
+cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots,
+                        cudaStream_t st);
+cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj, size_t m,
+                              uint32_t n, uint32_t* flags, int sms, cudaStream_t st);
+}  // namespace og
+
+using namespace og;
+
+namespace {
+
+thread_local char g_cuda_msg[512] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? OG_E_OOM : OG_E_CUDA;
+}
+
+#define CK(x)                                          \
+  do {                                                 \
+    cudaError_t _e = (x);                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, #x);   \
+  } while (0)
+
+#define TRY(x)                    \
+  do {                            \
+    int _r = (x);                 \
+    if (_r != OG_OK) return _r;   \
+  } while (0)
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t b) {
+    if (b <= bytes && p) return OG_OK;
+    release();
+    cudaError_t e = cudaMalloc(&p, b ? b : 16);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "cudaMalloc");
+    }
+    bytes = b;
+    return OG_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct HBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t b) {
+    if (b <= bytes && p) return OG_OK;
+    release();
+    cudaError_t e = cudaMallocHost(&p, b ? b : 16);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "cudaMallocHost");
+    }
+    bytes = b;
+    return OG_OK;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Device scratch of one launch configuration (grown on demand, reused across calls).
+struct Workspace {
+  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots;
+  HBuf h_qd, h_qs, h_sync, h_stats, h_slots;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void release() {
+    for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots})
+      b->release();
+    for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots}) b->release();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    e0 = e1 = nullptr;
+  }
+  int events() {
+    if (!e0) CK(cudaEventCreate(&e0));
+    if (!e1) CK(cudaEventCreate(&e1));
+    return OG_OK;
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+uint32_t pow2_floor(double x) {
+  if (!(x >= 1.0)) return 1u;
+  if (x >= 2147483648.0) return 1u << 31;
+  uint32_t p = 1;
+  while ((double)p * 2.0 <= x) p <<= 1;
+  return p;
+}
+
+uint32_t pow2_ceil(uint64_t x) {
+  uint32_t p = 1;
+  while (p < x && p < (1u << 31)) p <<= 1;
+  return p;
+}
+
+constexpr uint32_t kDefaultFusion = 1024;
+constexpr uint32_t kDefaultTile = 512;
+constexpr uint32_t kBinCap = 2048;
+constexpr uint64_t kDefaultSpinNs = 2000000000ull;
+
+}  // namespace
+
+struct og_graph {
+  uint32_t n = 0;
+  uint64_t m = 0;
+  uint32_t min_w = 0, max_w = 0;
+  double mean_w = 0.0;
+  uint32_t* off = nullptr;
+  uint2* adj = nullptr;
+  float2* xy = nullptr;
+  std::vector<float> h_xy;   // host copy: target coordinates of A* queries
+  bool xy_integral = false;
+  og_config cfg{};
+  Workspace ws;
+  int sms = 0;
+  int occ = 0;
+};
+
+struct og_server {
+  og_graph* g = nullptr;
+  og_config cfg{};
+  cudaStream_t stream = nullptr;
+  uint32_t slots = 0, B = 0, cap = 0, ocap = 0;
+  Workspace ws;
+  std::vector<QDesc> hq;
+  std::vector<uint64_t> tags;
+  std::vector<uint8_t> state;   // 0 free, 1 admitted (not started), 2 running, 3 finished
+  std::vector<uint32_t> results;
+  std::vector<uint32_t> free_list;
+  std::vector<uint32_t> pending;
+  std::deque<uint32_t> done;
+  bool started = false;
+};
+
+namespace {
+
+uint32_t default_delta(const og_graph* g) {
+  const double avg_deg = g->n ? (double)g->m / g->n : 0.0;
+  const double mw = g->mean_w > 0 ? g->mean_w : 1.0;
+  // Low-degree, large-diameter graphs want a wide bucket for parallelism; dense
+  // small-diameter graphs a narrow one for work efficiency (Section 6.2, Delta selection).
+  return avg_deg <= 8.0 ? pow2_floor(16.0 * mw) : pow2_floor(std::max(1.0, mw / 4.0));
+}
+
+// Effective schedule: explicit call config, then graph default, then library default.
+og_config resolve(const og_graph* g, const og_config* user) {
+  og_config d;
+  og_config_default(&d);
+  og_config r = d;
+  auto pick32 = [](uint32_t a, uint32_t b, uint32_t c) { return a ? a : (b ? b : c); };
+  auto pick64 = [](uint64_t a, uint64_t b, uint64_t c) { return a ? a : (b ? b : c); };
+  const og_config z{};
+  const og_config& u = user ? *user : z;
+  r.delta = pick32(u.delta, g->cfg.delta, default_delta(g));
+  r.fusion_threshold = pick32(u.fusion_threshold, g->cfg.fusion_threshold, kDefaultFusion);
+  r.expand_tile = pick32(u.expand_tile, g->cfg.expand_tile, kDefaultTile);
+  r.blocks_per_sm = pick32(u.blocks_per_sm, g->cfg.blocks_per_sm, 0);
+  r.ring_buckets = pick32(u.ring_buckets, g->cfg.ring_buckets, 0);
+  r.spin_limit_ns = pick64(u.spin_limit_ns, g->cfg.spin_limit_ns, kDefaultSpinNs);
+  r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
+  return r;
+}
+
+uint32_t ring_size(const og_graph* g, const og_config& c, uint32_t min_delta) {
+  if (c.ring_buckets) {
+    uint32_t b = pow2_ceil(c.ring_buckets);
+    return std::max(2u, std::min<uint32_t>(b, kMaxRing));
+  }
+  // Enough materialised buckets that one relaxation never jumps past the ring.
+  const uint64_t span = (uint64_t)g->max_w / std::max(1u, min_delta) + 2;
+  return std::max(2u, std::min<uint32_t>(pow2_ceil(span), kMaxRing));
+}
+
+int occupancy(og_graph* g, size_t smem) {
+  if (!g->occ) {
+    int dev = 0, b = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(delta_occupancy(&b, smem));
+    if (b < 1) {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "persistent kernel does not fit on an SM");
+      return OG_E_CUDA;
+    }
+    g->occ = b;
+  }
+  return OG_OK;
+}
+
+struct RunOut {
+  uint32_t err = 0;
+  uint64_t restarts = 0;
+};
+
+// Runs up to kMaxQ queries in one persistent launch, regrowing the arena when a query
+// runs out of bucket space.  dist_dev: nq*n device words (query i at + i*n).
+int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
+              uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)kBinCap * (sizeof(uint2) + sizeof(uint16_t));
+  TRY(occupancy(g, smem));
+  uint32_t min_delta = 0xFFFFFFFFu;
+  bool astar = false;
+  for (uint32_t i = 0; i < nq; ++i) {
+    min_delta = std::min(min_delta, qd[i].delta);
+    astar |= qd[i].kind == kASTAR;
+  }
+  const uint32_t B = ring_size(g, c, min_delta);
+  uint64_t entries = c.arena_entries ? c.arena_entries
+                                     : std::max<uint64_t>(6ull * g->n, 1ull << 16);
+  TRY(ws.events());
+  TRY(ws.h_qd.ensure(sizeof(QDesc) * nq));
+  TRY(ws.h_qs.ensure(sizeof(QState) * nq));
+  TRY(ws.h_sync.ensure(sizeof(Sync)));
+  TRY(ws.h_stats.ensure(sizeof(Stats)));
+  memcpy(ws.h_qd.p, qd, sizeof(QDesc) * nq);
+  std::vector<uint32_t> pending(nq);
+  for (uint32_t i = 0; i < nq; ++i) pending[i] = i;
+
+  for (int attempt = 0;; ++attempt) {
+    const uint64_t cap64 = std::max<uint64_t>(64, entries / 2 / B);
+    const uint64_t ocap64 = std::max<uint64_t>(64, entries / 4);
+    if (cap64 >= 0xFFFFFFF0ull || ocap64 >= 0xFFFFFFF0ull) return OG_E_ARENA;
+    const uint32_t cap = (uint32_t)cap64, ocap = (uint32_t)ocap64;
+    const uint32_t np = (uint32_t)pending.size();
+    TRY(ws.ring.ensure(sizeof(uint2) * (size_t)nq * B * cap));
+    TRY(ws.counts.ensure(sizeof(uint32_t) * (size_t)nq * B));
+    TRY(ws.ovf.ensure(sizeof(uint2) * (size_t)nq * 2 * ocap));
+    TRY(ws.qs.ensure(sizeof(QState) * nq));
+    TRY(ws.qd.ensure(sizeof(QDesc) * nq));
+    TRY(ws.pref.ensure(sizeof(uint32_t) * (nq + 1)));
+    TRY(ws.sync.ensure(sizeof(Sync)));
+    TRY(ws.stats.ensure(sizeof(Stats)));
+    TRY(ws.slots.ensure(sizeof(uint32_t) * nq));
+    TRY(ws.h_slots.ensure(sizeof(uint32_t) * nq));
+    memcpy(ws.h_slots.p, pending.data(), sizeof(uint32_t) * np);
+
+    Params P{};
+    P.off = g->off;
+    P.adj = g->adj;
+    P.xy = g->xy;
+    P.n = g->n;
+    P.xy_integral = g->xy_integral ? 1u : 0u;
+    P.dist = dist_dev;
+    P.qd = ws.qd.as<QDesc>();
+    P.qs = ws.qs.as<QState>();
+    P.ring = ws.ring.as<uint2>();
+    P.counts = ws.counts.as<uint32_t>();
+    P.ovf = ws.ovf.as<uint2>();
+    P.fr_pref = ws.pref.as<uint32_t>();
+    P.sync = ws.sync.as<Sync>();
+    P.stats = ws.stats.as<Stats>();
+    P.nq = nq;
+    P.B = B;
+    P.Bmask = B - 1;
+    P.cap = cap;
+    P.ocap = ocap;
+    P.T = c.fusion_threshold == OG_FUSION_OFF ? 0u : c.fusion_threshold;
+    P.tile = std::max<uint32_t>(32, (c.expand_tile + 31) / 32 * 32);
+    P.bin_cap = kBinCap;
+    P.max_rounds = 0xFFFFFFFFu;
+    P.has_astar = astar ? 1u : 0u;
+    P.spin_ns = c.spin_limit_ns;
+
+    CK(cudaMemcpyAsync(ws.qd.p, ws.h_qd.p, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.slots.p, ws.h_slots.p, sizeof(uint32_t) * np,
+                       cudaMemcpyHostToDevice, st));
+    if (attempt == 0) CK(cudaMemsetAsync(ws.qs.p, 0, sizeof(QState) * nq, st));
+    CK(cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), st));
+    CK(cudaMemsetAsync(ws.stats.p, 0, sizeof(Stats), st));
+    CK(launch_fill(dist_dev, g->n, ws.slots.as<uint32_t>(), np, g->sms, st));
+    CK(launch_init(P, ws.slots.as<uint32_t>(), np, st));
+    const int bps = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, g->occ) : g->occ;
+    CK(cudaEventRecord(ws.e0, st));
+    CK(launch_delta(P, g->sms * bps, smem, st));
+    CK(cudaEventRecord(ws.e1, st));
+    CK(cudaMemcpyAsync(ws.h_sync.p, ws.sync.p, sizeof(Sync), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_stats.p, ws.stats.p, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_qs.p, ws.qs.p, sizeof(QState) * nq, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ws.e0, ws.e1));
+    const Stats* hs = ws.h_stats.as<Stats>();
+    for (int k = 0; k < 16; ++k) acc->v[k] += hs->v[k];
+    acc->v[15] += (unsigned long long)(ms * 1.0e6);  // kernel ns (slot 15)
+    const Sync* hy = ws.h_sync.as<Sync>();
+    const QState* hq = ws.h_qs.as<QState>();
+    ro->err |= hy->err & ~(uint32_t)kErrArena;
+    if (hy->err & kErrTimeout) return OG_E_TIMEOUT;
+    pending.clear();
+    for (uint32_t i = 0; i < nq; ++i)
+      if (hq[i].aborted) pending.push_back(i);
+    for (uint32_t i = 0; i < nq; ++i)
+      if (!hq[i].aborted && d_out) d_out[i] = qd[i].kind == kSSSP ? 0u : hq[i].result;
+    if (pending.empty()) break;
+    // Some queries ran out of bucket space: rerun just those with twice the arena.
+    if (attempt >= 6) return OG_E_ARENA;
+    entries *= 2;
+    ro->restarts++;
+  }
+  return OG_OK;
+}
+
+void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
+  if (!out) return;
+  memset(out, 0, sizeof(*out));
+  out->rounds = s.v[kStRounds];
+  out->fused_iters = s.v[kStFused];
+  out->items = s.v[kStItems];
+  out->stale = s.v[kStStale];
+  out->relax = s.v[kStRelax];
+  out->improved = s.v[kStImproved];
+  out->local_inserts = s.v[kStLocal];
+  out->global_inserts = s.v[kStGlobal];
+  out->overflow_inserts = s.v[kStOvf];
+  out->redistributions = s.v[kStRedist];
+  out->restarts = restarts;
+  out->kernel_ns = s.v[15];
+}
+
+int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d) {
+  if (q.src >= g->n) return OG_E_INVALID;
+  memset(d, 0, sizeof(*d));
+  d->src = q.src;
+  d->dst = kNone;
+  switch (q.kind) {
+    case OG_Q_SSSP:
+      d->kind = kSSSP;
+      d->delta = q.delta ? q.delta : c.delta;
+      break;
+    case OG_Q_WBFS:
+      if (g->m && g->min_w == 0) return OG_E_INVALID;  // wBFS needs positive weights
+      d->kind = kSSSP;
+      d->delta = 1;
+      break;
+    case OG_Q_PPSP:
+    case OG_Q_ASTAR:
+      if (q.dst >= g->n) return OG_E_INVALID;
+      if (q.kind == OG_Q_ASTAR && !g->xy) return OG_E_INVALID;
+      d->kind = q.kind == OG_Q_PPSP ? kPPSP : kASTAR;
+      d->dst = q.dst;
+      if (q.kind == OG_Q_ASTAR) {
+        d->tx = g->h_xy[2 * (size_t)q.dst];
+        d->ty = g->h_xy[2 * (size_t)q.dst + 1];
+      }
+      d->delta = q.delta ? q.delta : c.delta;
+      break;
+    default:
+      return OG_E_INVALID;
+  }
+  if (d->delta == 0) return OG_E_INVALID;
+  return OG_OK;
+}
+
+int run_queries(og_graph* g, const og_query* qv, uint32_t nq, const og_config* ucfg,
+                uint32_t* dist_out, uint32_t* d_out, og_stats* stats, cudaStream_t st) {
+  if (!g || !qv || nq == 0) return OG_E_INVALID;
+  const og_config c = resolve(g, ucfg);
+  std::vector<QDesc> qd(nq);
+  for (uint32_t i = 0; i < nq; ++i) TRY(make_desc(g, qv[i], c, &qd[i]));
+  const bool dev_out = dist_out && is_device_ptr(dist_out);
+  Stats acc;
+  memset(&acc, 0, sizeof(acc));
+  RunOut ro;
+  for (uint32_t base = 0; base < nq; base += kMaxQ) {
+    const uint32_t k = std::min<uint32_t>(kMaxQ, nq - base);
+    uint32_t* ddist;
+    if (dev_out) {
+      ddist = dist_out + (size_t)base * g->n;
+    } else {
+      TRY(g->ws.dist.ensure(sizeof(uint32_t) * (size_t)k * g->n));
+      ddist = g->ws.dist.as<uint32_t>();
+    }
+    TRY(run_chunk(g, g->ws, qd.data() + base, k, c, ddist, d_out ? d_out + base : nullptr,
+                  &acc, &ro, st));
+    if (dist_out && !dev_out) {
+      CK(cudaMemcpyAsync(dist_out + (size_t)base * g->n, ddist,
+                         sizeof(uint32_t) * (size_t)k * g->n, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  export_stats(acc, ro.restarts, stats);
+  if (ro.err & kErrSat) return OG_E_OVERFLOW;
+  return OG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int og_version(void) { return 100; }
+
+const char* og_strerror(int code) {
+  switch (code) {
+    case OG_OK: return "ok";
+    case OG_E_INVALID: return "invalid argument";
+    case OG_E_OOM: return "out of memory";
+    case OG_E_CUDA: return "CUDA runtime error";
+    case OG_E_OVERFLOW: return "distance overflow (saturated at 0xFFFFFFFE)";
+    case OG_E_TIMEOUT: return "bounded device wait timed out";
+    case OG_E_BUSY: return "no free slot";
+    case OG_E_ARENA: return "bucket arena exhausted";
+    default: return "unknown error";
+  }
+}
+
+const char* og_last_cuda_error(void) { return g_cuda_msg; }
+
+void og_config_default(og_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->fusion_threshold = kDefaultFusion;
+  c->expand_tile = kDefaultTile;
+  c->spin_limit_ns = kDefaultSpinNs;
+}
+
+int og_graph_upload(const uint64_t* offsets, const uint32_t* neighbors, const uint32_t* weights,
+                    uint32_t n, uint64_t m, void* stream, og_graph** out) {
+  if (!out) return OG_E_INVALID;
+  *out = nullptr;
+  if (!offsets || n == 0 || n == 0xFFFFFFFFu) return OG_E_INVALID;
+  if (m && (!neighbors || !weights)) return OG_E_INVALID;
+  if (offsets[0] != 0 || offsets[n] != m || m >= 0xFFFFFFFFull) return OG_E_INVALID;
+  for (uint32_t i = 0; i < n; ++i)
+    if (offsets[i + 1] < offsets[i]) return OG_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  og_graph* g = new (std::nothrow) og_graph();
+  if (!g) return OG_E_OOM;
+  g->n = n;
+  g->m = m;
+  auto fail = [&](int code) {
+    og_graph_free(g);
+    return code;
+  };
+  std::vector<uint32_t> off32(n + 1);
+  for (uint32_t i = 0; i <= n; ++i) off32[i] = (uint32_t)offsets[i];
+  double wsum = 0.0;
+  for (uint64_t e = 0; e < m; ++e) wsum += weights[e];
+  g->mean_w = m ? wsum / (double)m : 1.0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&g->off, sizeof(uint32_t) * (n + 1))) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMalloc offsets"));
+  if ((e = cudaMalloc(&g->adj, sizeof(uint2) * (m ? m : 1))) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMalloc adjacency"));
+  if ((e = cudaMemcpyAsync(g->off, off32.data(), sizeof(uint32_t) * (n + 1),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return fail(cuda_fail(e, "copy offsets"));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t* tmp = nullptr;
+  uint32_t* flags = nullptr;
+  if (m) {
+    if ((e = cudaMalloc(&tmp, sizeof(uint32_t) * 2 * m)) != cudaSuccess)
+      return fail(cuda_fail(e, "cudaMalloc staging"));
+    if ((e = cudaMalloc(&flags, sizeof(uint32_t) * 4)) != cudaSuccess) {
+      cudaFree(tmp);
+      return fail(cuda_fail(e, "cudaMalloc flags"));
+    }
+    const uint32_t init[4] = {0u, 0xFFFFFFFFu, 0u, 0u};
+    uint32_t hflags[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(tmp, neighbors, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp + m, weights, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_interleave(tmp, tmp + m, g->adj, m, n, flags, g->sms, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    cudaFree(flags);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "upload adjacency"));
+    if (hflags[0]) return fail(OG_E_INVALID);  // a neighbor id >= n
+    g->min_w = hflags[1];
+    g->max_w = hflags[2];
+  } else {
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "upload"));
+  }
+  og_config_default(&g->cfg);
+  g->cfg.fusion_threshold = 0;
+  g->cfg.expand_tile = 0;
+  g->cfg.spin_limit_ns = 0;
+  *out = g;
+  return OG_OK;
+}
+
+int og_graph_set_coords(og_graph* g, const float* xy, void* stream) {
+  if (!g || !xy) return OG_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<float> h(2 * (size_t)g->n);
+  if (is_device_ptr(xy)) {
+    CK(cudaMemcpyAsync(h.data(), xy, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    memcpy(h.data(), xy, sizeof(float) * h.size());
+  }
+  bool integral = true;
+  for (float v : h) {
+    if (!std::isfinite(v)) return OG_E_INVALID;
+    if (std::fabs(v) >= 16777216.0f || std::floor(v) != v) integral = false;
+  }
+  if (!g->xy) {
+    cudaError_t e = cudaMalloc(&g->xy, sizeof(float2) * g->n);
+    if (e != cudaSuccess) {
+      g->xy = nullptr;
+      return cuda_fail(e, "cudaMalloc coords");
+    }
+  }
+  CK(cudaMemcpyAsync(g->xy, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  g->xy_integral = integral;
+  g->h_xy.swap(h);
+  return OG_OK;
+}
+
+int og_graph_info(const og_graph* g, uint32_t* n, uint64_t* m, uint32_t* min_w,
+                  uint32_t* max_w) {
+  if (!g) return OG_E_INVALID;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (min_w) *min_w = g->min_w;
+  if (max_w) *max_w = g->max_w;
+  return OG_OK;
+}
+
+int og_graph_set_config(og_graph* g, const og_config* cfg) {
+  if (!g || !cfg) return OG_E_INVALID;
+  g->cfg = *cfg;
+  return OG_OK;
+}
+
+int og_graph_get_config(const og_graph* g, og_config* cfg) {
+  if (!g || !cfg) return OG_E_INVALID;
+  *cfg = resolve(g, nullptr);
+  return OG_OK;
+}
+
+void og_graph_free(og_graph* g) {
+  if (!g) return;
+  g->ws.release();
+  if (g->off) cudaFree(g->off);
+  if (g->adj) cudaFree(g->adj);
+  if (g->xy) cudaFree(g->xy);
+  delete g;
+}
+
+int og_query_run(og_graph* g, const og_query* q, const og_config* cfg, uint32_t* dist_out,
+                 uint32_t* d_out, og_stats* stats, void* stream) {
+  if (!g || !q) return OG_E_INVALID;
+  return run_queries(g, q, 1, cfg, dist_out, d_out, stats, (cudaStream_t)stream);
+}
+
+int og_sssp_delta(og_graph* g, uint32_t src, uint32_t delta, uint32_t* dist_out, void* stream) {
+  if (!dist_out) return OG_E_INVALID;
+  og_query q{OG_Q_SSSP, src, 0, delta};
+  return og_query_run(g, &q, nullptr, dist_out, nullptr, nullptr, stream);
+}
+
+int og_wbfs(og_graph* g, uint32_t src, uint32_t* dist_out, void* stream) {
+  if (!dist_out) return OG_E_INVALID;
+  og_query q{OG_Q_WBFS, src, 0, 1};
+  return og_query_run(g, &q, nullptr, dist_out, nullptr, nullptr, stream);
+}
+
+int og_ppsp(og_graph* g, uint32_t src, uint32_t dst, uint32_t delta, uint32_t* d_out,
+            void* stream) {
+  if (!d_out) return OG_E_INVALID;
+  og_query q{OG_Q_PPSP, src, dst, delta};
+  return og_query_run(g, &q, nullptr, nullptr, d_out, nullptr, stream);
+}
+
+int og_astar(og_graph* g, uint32_t src, uint32_t dst, const float* coords, uint32_t delta,
+             uint32_t* d_out, void* stream) {
+  if (!g || !d_out) return OG_E_INVALID;
+  if (coords) TRY(og_graph_set_coords(g, coords, stream));
+  og_query q{OG_Q_ASTAR, src, dst, delta};
+  return og_query_run(g, &q, nullptr, nullptr, d_out, nullptr, stream);
+}
+
+int og_batch_run(og_graph* g, const og_query* q, uint32_t nq, const og_config* cfg,
+                 uint32_t* dist_out, uint32_t* d_out, og_stats* stats, void* stream) {
+  return run_queries(g, q, nq, cfg, dist_out, d_out, stats, (cudaStream_t)stream);
+}
+
+// ---- serving ------------------------------------------------------------------------------
+
+int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void* stream,
+                     og_server** out) {
+  if (!g || !out) return OG_E_INVALID;
+  *out = nullptr;
+  og_server* s = new (std::nothrow) og_server();
+  if (!s) return OG_E_OOM;
+  s->g = g;
+  s->cfg = resolve(g, cfg);
+  s->stream = (cudaStream_t)stream;
+  const uint32_t B = ring_size(g, s->cfg, s->cfg.delta);
+  const uint64_t entries = s->cfg.arena_entries
+                               ? s->cfg.arena_entries
+                               : std::max<uint64_t>((uint64_t)g->n / 2, 1ull << 20);
+  const uint64_t per_slot = sizeof(uint32_t) * (uint64_t)g->n + sizeof(uint2) * entries +
+                            sizeof(QState) + sizeof(QDesc) + 64;
+  uint32_t slots = max_slots;
+  if (!slots) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return OG_E_CUDA;
+    }
+    slots = (uint32_t)std::min<uint64_t>(kMaxQ, (uint64_t)(fr / 2) / per_slot);
+    if (!slots) {
+      delete s;
+      return OG_E_OOM;
+    }
+  }
+  if (slots > (uint32_t)kMaxQ) slots = kMaxQ;
+  s->slots = slots;
+  s->B = B;
+  s->cap = (uint32_t)std::max<uint64_t>(64, entries / 2 / B);
+  s->ocap = (uint32_t)std::max<uint64_t>(64, entries / 4);
+  Workspace& ws = s->ws;
+  int r = OG_OK;
+  if (r == OG_OK) r = ws.dist.ensure(sizeof(uint32_t) * (size_t)slots * g->n);
+  if (r == OG_OK) r = ws.ring.ensure(sizeof(uint2) * (size_t)slots * B * s->cap);
+  if (r == OG_OK) r = ws.counts.ensure(sizeof(uint32_t) * (size_t)slots * B);
+  if (r == OG_OK) r = ws.ovf.ensure(sizeof(uint2) * (size_t)slots * 2 * s->ocap);
+  if (r == OG_OK) r = ws.qs.ensure(sizeof(QState) * slots);
+  if (r == OG_OK) r = ws.qd.ensure(sizeof(QDesc) * slots);
+  if (r == OG_OK) r = ws.pref.ensure(sizeof(uint32_t) * (slots + 1));
+  if (r == OG_OK) r = ws.sync.ensure(sizeof(Sync));
+  if (r == OG_OK) r = ws.stats.ensure(sizeof(Stats));
+  if (r == OG_OK) r = ws.slots.ensure(sizeof(uint32_t) * slots);
+  if (r == OG_OK) r = ws.h_qd.ensure(sizeof(QDesc) * slots);
+  if (r == OG_OK) r = ws.h_qs.ensure(sizeof(QState) * slots);
+  if (r == OG_OK) r = ws.h_sync.ensure(sizeof(Sync));
+  if (r == OG_OK) r = ws.h_slots.ensure(sizeof(uint32_t) * slots);
+  if (r == OG_OK) r = ws.events();
+  if (r == OG_OK && cudaMemsetAsync(ws.qs.p, 0, sizeof(QState) * slots, s->stream) != cudaSuccess)
+    r = OG_E_CUDA;
+  if (r == OG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = OG_E_CUDA;
+  if (r != OG_OK) {
+    og_server_free(s);
+    return r;
+  }
+  s->hq.assign(slots, QDesc{});
+  s->tags.assign(slots, 0);
+  s->state.assign(slots, 0);
+  s->results.assign(slots, kInf);
+  for (uint32_t i = slots; i > 0; --i) s->free_list.push_back(i - 1);
+  *out = s;
+  return OG_OK;
+}
+
+int og_server_submit(og_server* s, const og_query* q, uint64_t tag) {
+  if (!s || !q) return OG_E_INVALID;
+  if (s->free_list.empty()) return OG_E_BUSY;
+  QDesc d;
+  TRY(make_desc(s->g, *q, s->cfg, &d));
+  const uint32_t slot = s->free_list.back();
+  s->free_list.pop_back();
+  s->hq[slot] = d;
+  s->tags[slot] = tag;
+  s->state[slot] = 1;
+  s->pending.push_back(slot);
+  return OG_OK;
+}
+
+int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active) {
+  if (!s) return OG_E_INVALID;
+  og_graph* g = s->g;
+  Workspace& ws = s->ws;
+  cudaStream_t st = s->stream;
+  const size_t smem = 2 * (size_t)kBinCap * (sizeof(uint2) + sizeof(uint16_t));
+  TRY(occupancy(g, smem));
+  bool astar = false;
+  uint32_t running = 0;
+  for (uint32_t i = 0; i < s->slots; ++i) {
+    if (s->state[i] == 1 || s->state[i] == 2) {
+      ++running;
+      astar |= s->hq[i].kind == kASTAR;
+    }
+  }
+  if (n_active) *n_active = running;
+  if (!running) return OG_OK;
+  Params P{};
+  P.off = g->off;
+  P.adj = g->adj;
+  P.xy = g->xy;
+  P.n = g->n;
+  P.xy_integral = g->xy_integral ? 1u : 0u;
+  P.dist = ws.dist.as<uint32_t>();
+  P.qd = ws.qd.as<QDesc>();
+  P.qs = ws.qs.as<QState>();
+  P.ring = ws.ring.as<uint2>();
+  P.counts = ws.counts.as<uint32_t>();
+  P.ovf = ws.ovf.as<uint2>();
+  P.fr_pref = ws.pref.as<uint32_t>();
+  P.sync = ws.sync.as<Sync>();
+  P.stats = ws.stats.as<Stats>();
+  P.nq = s->slots;
+  P.B = s->B;
+  P.Bmask = s->B - 1;
+  P.cap = s->cap;
+  P.ocap = s->ocap;
+  P.T = s->cfg.fusion_threshold == OG_FUSION_OFF ? 0u : s->cfg.fusion_threshold;
+  P.tile = std::max<uint32_t>(32, (s->cfg.expand_tile + 31) / 32 * 32);
+  P.bin_cap = kBinCap;
+  P.max_rounds = max_rounds ? max_rounds : 0xFFFFFFFFu;
+  P.has_astar = astar ? 1u : 0u;
+  P.spin_ns = s->cfg.spin_limit_ns;
+  const uint32_t np = (uint32_t)s->pending.size();
+  if (np) {
+    QDesc* hqd = ws.h_qd.as<QDesc>();
+    memcpy(hqd, s->hq.data(), sizeof(QDesc) * s->slots);
+    memcpy(ws.h_slots.p, s->pending.data(), sizeof(uint32_t) * np);
+    CK(cudaMemcpyAsync(ws.qd.p, hqd, sizeof(QDesc) * s->slots, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.slots.p, ws.h_slots.p, sizeof(uint32_t) * np,
+                       cudaMemcpyHostToDevice, st));
+    CK(launch_fill(P.dist, g->n, ws.slots.as<uint32_t>(), np, g->sms, st));
+    CK(launch_init(P, ws.slots.as<uint32_t>(), np, st));
+    for (uint32_t slot : s->pending) s->state[slot] = 2;
+    s->pending.clear();
+  }
+  CK(cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), st));
+  CK(cudaMemsetAsync(ws.stats.p, 0, sizeof(Stats), st));
+  const int bps = s->cfg.blocks_per_sm ? std::min<int>((int)s->cfg.blocks_per_sm, g->occ) : g->occ;
+  CK(launch_delta(P, g->sms * bps, smem, st));
+  CK(cudaMemcpyAsync(ws.h_sync.p, ws.sync.p, sizeof(Sync), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ws.h_qs.p, ws.qs.p, sizeof(QState) * s->slots, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const Sync* hy = ws.h_sync.as<Sync>();
+  if (hy->err & kErrTimeout) return OG_E_TIMEOUT;
+  const QState* hq = ws.h_qs.as<QState>();
+  running = 0;
+  for (uint32_t i = 0; i < s->slots; ++i) {
+    if (s->state[i] != 2) continue;
+    if (hq[i].active) {
+      ++running;
+      continue;
+    }
+    if (hq[i].aborted) {
+      // Arena too small for this query: answer it alone with a growing arena.
+      og_query q{s->hq[i].kind == kASTAR ? (uint32_t)OG_Q_ASTAR
+                 : s->hq[i].kind == kPPSP ? (uint32_t)OG_Q_PPSP : (uint32_t)OG_Q_SSSP,
+                 s->hq[i].src, s->hq[i].dst, s->hq[i].delta};
+      uint32_t d = kInf;
+      TRY(run_queries(g, &q, 1, &s->cfg, nullptr, &d, nullptr, st));
+      s->results[i] = d;
+    } else {
+      s->results[i] = s->hq[i].kind == kSSSP ? 0u : hq[i].result;
+    }
+    s->state[i] = 3;
+    s->done.push_back(i);
+  }
+  if (n_active) *n_active = running + (uint32_t)s->pending.size();
+  if (hy->err & kErrSat) return OG_E_OVERFLOW;
+  return OG_OK;
+}
+
+int og_server_poll(og_server* s, uint64_t* tags, uint32_t* d_out, uint32_t cap,
+                   uint32_t* n_done) {
+  if (!s || !n_done) return OG_E_INVALID;
+  uint32_t k = 0;
+  while (k < cap && !s->done.empty()) {
+    const uint32_t slot = s->done.front();
+    s->done.pop_front();
+    if (tags) tags[k] = s->tags[slot];
+    if (d_out) d_out[k] = s->results[slot];
+    s->state[slot] = 0;
+    s->free_list.push_back(slot);
+    ++k;
+  }
+  *n_done = k;
+  return OG_OK;
+}
+
+int og_server_slots(const og_server* s, uint32_t* max_slots, uint32_t* n_free) {
+  if (!s) return OG_E_INVALID;
+  if (max_slots) *max_slots = s->slots;
+  if (n_free) *n_free = (uint32_t)s->free_list.size();
+  return OG_OK;
+}
+
+void og_server_free(og_server* s) {
+  if (!s) return;
+  s->ws.release();
+  delete s;
+}
+
+// ---- autotuning ---------------------------------------------------------------------------
+
+int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t* dsts,
+                uint32_t nsample, uint32_t delta_lo, uint32_t delta_hi, og_config* out) {
+  if (!g || !srcs || nsample == 0 || kind > OG_Q_WBFS) return OG_E_INVALID;
+  if ((kind == OG_Q_PPSP || kind == OG_Q_ASTAR) && !dsts) return OG_E_INVALID;
+  std::vector<og_query> qs(nsample);
+  for (uint32_t i = 0; i < nsample; ++i)
+    qs[i] = og_query{kind, srcs[i], dsts ? dsts[i] : 0u, 0u};
+  og_config base = resolve(g, nullptr);
+  // Times one candidate: a warm-up run, then the device time of a second run.
+  auto measure = [&](const og_config& c, double* ns) -> int {
+    og_stats st;
+    for (int rep = 0; rep < 2; ++rep)
+      TRY(run_queries(g, qs.data(), nsample, &c, nullptr, nullptr, &st, nullptr));
+    *ns = (double)st.kernel_ns;
+    return OG_OK;
+  };
+  og_config best = base;
+  double best_ns = 0;
+  TRY(measure(best, &best_ns));
+  if (kind != OG_Q_WBFS) {
+    if (!delta_lo) delta_lo = std::max(1u, default_delta(g) / 64);
+    if (!delta_hi) delta_hi = std::max(delta_lo, default_delta(g) * 8);
+    for (uint64_t d = pow2_ceil(delta_lo); d <= delta_hi; d *= 2) {
+      og_config c = best;
+      c.delta = (uint32_t)d;
+      double ns;
+      TRY(measure(c, &ns));
+      if (ns < best_ns) { best_ns = ns; best = c; }
+    }
+  }
+  const uint32_t fusions[] = {OG_FUSION_OFF, 64, 256, 1024, 2048, 0xFFFFFFFFu};
+  for (uint32_t f : fusions) {
+    og_config c = best;
+    c.fusion_threshold = f;
+    double ns;
+    TRY(measure(c, &ns));
+    if (ns < best_ns) { best_ns = ns; best = c; }
+  }
+  const uint32_t tiles[] = {128, 256, 512, 1024, 2048};
+  for (uint32_t t : tiles) {
+    og_config c = best;
+    c.expand_tile = t;
+    double ns;
+    TRY(measure(c, &ns));
+    if (ns < best_ns) { best_ns = ns; best = c; }
+  }
+  for (uint32_t b = 1; b <= (uint32_t)g->occ; ++b) {
+    og_config c = best;
+    c.blocks_per_sm = b;
+    double ns;
+    TRY(measure(c, &ns));
+    if (ns < best_ns) { best_ns = ns; best = c; }
+  }
+  g->cfg = best;
+  if (out) *out = best;
+  return OG_OK;
+}
+
+}  // extern "C"

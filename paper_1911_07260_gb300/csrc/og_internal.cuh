@@ -1,0 +1,108 @@
+// Internal device structures of libog (not part of the ABI).
+//
+// Layout in HBM (one launch serves nq queries; query q is a "slot"):
+//   off    uint32[n+1]      CSR offsets (read-only)
+//   adj    uint2[m]         {neighbor, weight} pairs, one 8-byte load per edge
+//   xy     float2[n]        coordinates (A* only)
+//   dist   uint32[nq][n]    priority vector per query (Section 4.1: the dist vector)
+//   ring   uint2[nq][B][cap]  materialised buckets: entries {vertex, dist at insert}
+//   counts uint32[nq][B]    append counters of the ring slots
+//   ovf    uint2[nq][2][ocap] overflow pile (double-buffered for redistribution)
+//   qs     QState[nq]       bucket cursor of each query
+//   sync   Sync             grid-barrier words, phase, error bits
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace og {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;   // unreachable
+constexpr uint32_t kSat = 0xFFFFFFFEu;   // saturated distance
+constexpr uint32_t kNone = 0xFFFFFFFFu;  // no target
+constexpr int kBlock = 256;              // threads per persistent CTA
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxQ = 512;               // queries per launch
+constexpr int kMaxRing = 64;             // materialised buckets per query
+
+enum Kind : uint32_t { kSSSP = 0, kPPSP = 1, kASTAR = 2 };
+
+enum Phase : uint32_t {
+  kPhRelax = 0,      // process the current buckets (frontier pass + fused local loop)
+  kPhRedistMin = 1,  // overflow pile: smallest live bucket
+  kPhRedistMove = 2, // overflow pile: move entries of the new ring window into the ring
+  kPhStop = 3,
+  kPhPrologue = 4,   // kernel start: publish the frontier of the current state
+};
+
+enum ErrBits : uint32_t { kErrTimeout = 1, kErrArena = 2, kErrSat = 4 };
+// A timeout stops the launch; an exhausted arena only stops the query that hit it.
+constexpr uint32_t kErrFatal = kErrTimeout;
+
+struct QDesc {
+  uint32_t src, dst, delta, kind;
+  float tx, ty;          // target coordinates (A*)
+  uint32_t pad0, pad1;
+};
+
+struct QState {
+  uint32_t cur;          // current bucket index
+  uint32_t head, tail;   // frontier = ring slot(cur) positions [head, tail)
+  uint32_t active;       // 1 while the query runs
+  uint32_t ovf_n;        // entries appended to the active overflow pile
+  uint32_t ovf_min;      // smallest bucket appended to it since the last redistribution
+  uint32_t ovf_sel;      // active pile (0 / 1)
+  uint32_t redist;       // redistribution in progress
+  uint32_t ovf_n2, ovf_min2;  // the other pile during a redistribution
+  uint32_t redist_min;   // smallest live bucket found by the redistribution
+  uint32_t no_exit;      // A*: early exit disabled (a key fell below the cursor)
+  uint32_t result;       // dist(src, dst) once finished
+  uint32_t aborted;      // bucket arena exhausted: the query stopped early
+  uint32_t pad[2];
+};
+
+struct Sync {
+  uint32_t arrive;       // barrier arrivals
+  uint32_t gen;          // barriers released in this launch
+  uint32_t err;          // ErrBits (sticky)
+  uint32_t phase;        // phase to run after the barrier
+  uint32_t work;         // frontier tiles claimed in this phase
+  uint32_t total;        // frontier entries in this phase
+  uint32_t rounds;       // rounds run in this launch
+  uint32_t any_active;
+  uint32_t pad[8];
+};
+
+enum StatIdx {
+  kStRounds, kStFused, kStItems, kStStale, kStRelax, kStImproved, kStLocal, kStGlobal,
+  kStOvf, kStRedist, kStCount
+};
+struct Stats { unsigned long long v[16]; };
+
+struct Params {
+  const uint32_t* off;
+  const uint2* adj;
+  const float2* xy;
+  uint32_t n;
+  uint32_t xy_integral;   // coordinates integral and < 2^24 in magnitude
+  uint32_t* dist;         // nq * n
+  const QDesc* qd;
+  QState* qs;
+  uint2* ring;
+  uint32_t* counts;
+  uint2* ovf;
+  uint32_t* fr_pref;      // nq + 1 prefix sums of the frontier sizes
+  Sync* sync;
+  Stats* stats;
+  uint32_t nq;
+  uint32_t B, Bmask;
+  uint32_t cap;           // entries per ring slot
+  uint32_t ocap;          // entries per overflow pile
+  uint32_t T;             // fusion threshold (0 = off)
+  uint32_t tile;          // frontier entries per CTA grab
+  uint32_t bin_cap;       // CTA-local bin capacity per buffer
+  uint32_t max_rounds;    // stop (resumably) after this many rounds
+  uint32_t has_astar;
+  unsigned long long spin_ns;
+};
+
+}  // namespace og

@@ -1,0 +1,763 @@
+// Device side of libog: Delta-stepping with eager bucket update and bucket fusion.
+//
+// Mapping of the paper's method (Section 3.2 / 3.3, figure "SSSP with the eager bucket
+// update approach and the bucket fusion optimization") onto one persistent,
+// cooperatively launched kernel:
+//   * the thread-local buckets of the paper become CTA-local bins in shared memory for
+//     the current bucket, plus per-query materialised global buckets (a ring of B device
+//     arrays) and one overflow pile for buckets beyond the ring;
+//   * one "round" = every CTA claims tiles of the current bucket's global frontier and
+//     relaxes their out-edges (atomicMin on the uint32 distance; an improved vertex is
+//     appended to bucket floor(d / Delta) -- the eager update), then runs the fusion
+//     loop: while its local bin of the current bucket is non-empty and smaller than the
+//     threshold it processes that bin with block-level synchronisation only; a bin that
+//     reaches the threshold is copied to the global bucket so the next round spreads it
+//     over all CTAs;
+//   * between rounds a bounded grid barrier runs; the CTA that arrives last picks the
+//     next bucket of every query (the smallest non-empty one, scanned with a warp ballot)
+//     and applies the PPSP / A* stop rule before it releases the others.
+#include "og_internal.cuh"
+
+namespace og {
+
+#define FULL 0xffffffffu
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// A* heuristic floor(100 * Euclidean distance to the target).  Integral coordinates:
+// exact integer square root of 10000 * (dx^2 + dy^2) (double estimate, then corrected
+// so that s^2 <= N < (s+1)^2).  Otherwise a double evaluation minus one unit, which stays
+// below the exact value.
+__device__ __forceinline__ uint32_t heuristic(const Params& P, uint32_t v, float tx, float ty) {
+  const float2 p = __ldg(P.xy + v);
+  if (P.xy_integral) {
+    const long long dx = (long long)p.x - (long long)tx;
+    const long long dy = (long long)p.y - (long long)ty;
+    const unsigned long long N = 10000ull * (unsigned long long)(dx * dx + dy * dy);
+    unsigned long long s = (unsigned long long)sqrt((double)N);
+    while (s * s > N) --s;
+    while ((s + 1) * (s + 1) <= N) ++s;
+    return s >= kSat ? kSat - 1 : (uint32_t)s;
+  }
+  const double dx = (double)p.x - (double)tx, dy = (double)p.y - (double)ty;
+  const double d = floor(100.0 * sqrt(dx * dx + dy * dy)) - 1.0;
+  if (!(d > 0.0)) return 0u;
+  return d >= 4.0e9 ? 4000000000u : (uint32_t)d;
+}
+
+// Priority coarsening (Section 2): bucket = floor(priority / Delta); A* priority is g + h.
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t h, uint32_t delta) {
+  if (h == 0) return d / delta;
+  return (uint32_t)(((unsigned long long)d + h) / delta);
+}
+
+struct Smem {
+  uint32_t cur[kMaxQ];     // current bucket per query
+  uint32_t delta[kMaxQ];
+  uint32_t head[kMaxQ];    // frontier start in the current ring slot
+  uint32_t pref[kMaxQ + 1];// frontier prefix sums (scratch in the decider)
+  uint32_t binN[2];        // CTA-local bin fill counts
+  uint32_t grab;
+  uint32_t last;
+  uint32_t phase;
+  uint32_t err;
+  uint32_t f_active, f_redist;
+  uint32_t wtmp[kWarps + 1];
+};
+
+struct Bins {
+  uint2* e[2];
+  uint16_t* q[2];
+};
+
+struct Cnt {
+  uint32_t items, stale, relax, improved, local, global, ovf;
+};
+
+// Appends the improved vertices of a warp (lanes with ins) to their buckets: the CTA-local
+// bin when the bucket is the query's current one and fusion is on, else the ring slot of
+// the bucket (warp-aggregated: lanes with the same (query, slot) share one atomicAdd),
+// else the overflow pile.  Must be called by all 32 lanes.
+__device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins& B, int out,
+                                            bool ins, bool allow_local, uint32_t v,
+                                            uint32_t nd, uint32_t key, uint32_t q, Cnt& C) {
+  const uint32_t lane = threadIdx.x & 31;
+  int dest = 0;  // 0 none, 1 local bin, 2 ring, 3 overflow
+  if (ins) {
+    const uint32_t cq = S.cur[q];
+    if (key < cq) {  // only with an inconsistent A* heuristic: clamp, disable early exit
+      key = cq;
+      P.qs[q].no_exit = 1u;
+    }
+    dest = (allow_local && key == cq) ? 1 : ((key - cq < P.B) ? 2 : 3);
+  }
+  const unsigned lm = __ballot_sync(FULL, dest == 1);
+  if (lm) {
+    const int leader = __ffs(lm) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(&S.binN[out], (uint32_t)__popc(lm));
+    base = __shfl_sync(FULL, base, leader);
+    if (dest == 1) {
+      const uint32_t pos = base + __popc(lm & lanemask_lt());
+      if (pos < P.bin_cap) {
+        B.e[out][pos] = make_uint2(v, nd);
+        B.q[out][pos] = (uint16_t)q;
+        C.local++;
+      } else {
+        dest = 2;  // bin full: the entry goes to the global current bucket
+      }
+    }
+  }
+  const unsigned rm = __ballot_sync(FULL, dest == 2);
+  if (dest == 2) {
+    const uint32_t cid = q * P.B + (key & P.Bmask);
+    const unsigned peers = __match_any_sync(rm, cid);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(P.counts + cid, (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const uint32_t pos = base + __popc(peers & lanemask_lt());
+    if (pos < P.cap) {
+      P.ring[(size_t)cid * P.cap + pos] = make_uint2(v, nd);
+      C.global++;
+    } else {
+      dest = 3;  // slot full: spill to the overflow pile
+    }
+  }
+  if (dest == 3) {
+    QState* s = P.qs + q;
+    const uint32_t sel = __ldcg(&s->ovf_sel);
+    const uint32_t pos = atomicAdd(&s->ovf_n, 1u);
+    atomicMin(&s->ovf_min, key);
+    if (pos < P.ocap) {
+      P.ovf[((size_t)q * 2 + sel) * P.ocap + pos] = make_uint2(v, nd);
+      C.ovf++;
+    } else {
+      s->aborted = 1u;
+      atomicOr(&P.sync->err, kErrArena);
+    }
+  }
+}
+
+// Relaxes one edge per lane (ok lanes): nd = g + w (saturating), atomicMin on dist[v];
+// an improvement is inserted eagerly into bucket floor((nd + h) / Delta).
+__device__ __forceinline__ void relax_warp(const Params& P, Smem& S, const Bins& B, int out,
+                                           bool allow_local, bool ok, uint32_t e, uint32_t g,
+                                           uint32_t q, Cnt& C) {
+  bool ins = false;
+  uint32_t v = 0, nd = 0, key = 0;
+  if (ok) {
+    const uint2 ew = __ldg(P.adj + e);
+    v = ew.x;
+    const unsigned long long s = (unsigned long long)g + ew.y;
+    nd = s >= kSat ? kSat : (uint32_t)s;
+    if (s >= kSat) atomicOr(&P.sync->err, kErrSat);
+    C.relax++;
+    uint32_t h = 0;
+    if (P.has_astar) {
+      const QDesc* d = P.qd + q;
+      if (__ldg(&d->kind) == kASTAR) h = heuristic(P, v, __ldg(&d->tx), __ldg(&d->ty));
+    }
+    const uint32_t old = atomicMin(P.dist + (size_t)q * P.n + v, nd);
+    if (nd < old) {
+      ins = true;
+      C.improved++;
+      key = bucket_of(nd, h, S.delta[q]);
+    }
+  }
+  insert_warp(P, S, B, out, ins, allow_local, v, nd, key, q, C);
+}
+
+// Expands the bucket entries held by a warp (one per lane with has): drops entries whose
+// vertex has a smaller distance by now (a newer entry exists), then relaxes all out-edges.
+// Vertices with >= 32 edges are expanded by the whole warp one at a time; the others are
+// flattened into one edge list that the 32 lanes walk together, so consecutive lanes
+// read consecutive edges of a vertex.  Must be called by all 32 lanes.
+__device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins& B, int out,
+                                            bool allow_local, bool has, uint32_t u,
+                                            uint32_t g, uint32_t q, Cnt& C) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t beg = 0, end = 0;
+  if (has) {
+    C.items++;
+    const uint32_t d = __ldcg(P.dist + (size_t)q * P.n + u);
+    beg = __ldg(P.off + u);
+    end = __ldg(P.off + u + 1);
+    if (d != g) {
+      has = false;
+      C.stale++;
+      beg = end = 0;
+    }
+  }
+  const uint32_t deg = end - beg;
+  const bool heavy = deg >= 32u;
+  unsigned hm = __ballot_sync(FULL, heavy);
+  while (hm) {
+    const int l = __ffs(hm) - 1;
+    hm &= hm - 1;
+    const uint32_t hb = __shfl_sync(FULL, beg, l), he = __shfl_sync(FULL, end, l);
+    const uint32_t hg = __shfl_sync(FULL, g, l), hq = __shfl_sync(FULL, q, l);
+    for (uint32_t e0 = hb; e0 < he; e0 += 32)
+      relax_warp(P, S, B, out, allow_local, e0 + lane < he, e0 + lane, hg, hq, C);
+  }
+  const uint32_t ld = heavy ? 0u : deg;
+  uint32_t incl = ld;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, incl, o);
+    if ((int)lane >= o) incl += t;
+  }
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  const uint32_t excl = incl - ld;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t idx = base + lane;
+    uint32_t pos = 0;  // owner lane: number of lanes whose inclusive sum is <= idx
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      const uint32_t x = __shfl_sync(FULL, incl, pos + s - 1);
+      if (x <= idx) pos += s;
+    }
+    const uint32_t ob = __shfl_sync(FULL, beg, pos), oe = __shfl_sync(FULL, excl, pos);
+    const uint32_t og = __shfl_sync(FULL, g, pos), oq = __shfl_sync(FULL, q, pos);
+    relax_warp(P, S, B, out, allow_local, idx < total, ob + (idx - oe), og, oq, C);
+  }
+}
+
+// Block-wide exclusive scan of a[0..n) (n <= 2 * kBlock) in place; a[n] = total.
+__device__ void block_exscan(uint32_t* a, uint32_t n, uint32_t* wtmp) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
+  const uint32_t x0 = i0 < n ? a[i0] : 0u, x1 = i1 < n ? a[i1] : 0u;
+  const uint32_t s = x0 + x1;
+  uint32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, incl, o);
+    if ((int)lane >= o) incl += t;
+  }
+  __syncthreads();
+  if (lane == 31) wtmp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < (uint32_t)kWarps ? wtmp[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, wi, o);
+      if ((int)lane >= o) wi += t;
+    }
+    __syncwarp();
+    if (lane < (uint32_t)kWarps) wtmp[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t ex = wtmp[warp] + incl - s;
+  if (i0 < n) a[i0] = ex;
+  if (i1 < n) a[i1] = ex + x0;
+  if (tid == kBlock - 1) a[n] = ex + s;
+  __syncthreads();
+}
+
+// Run by the CTA that arrives last at a grid barrier, before it releases the others:
+// advances every query's bucket cursor and publishes the next phase and frontier.
+__device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Sync* sy = P.sync;
+  const uint32_t err = ld_relaxed(&sy->err);
+  const bool fatal = (err & kErrFatal) != 0;
+  if (tid == 0) {
+    S.f_active = 0;
+    S.f_redist = 0;
+  }
+  __syncthreads();
+  for (uint32_t q = warp; q < P.nq; q += kWarps) {
+    QState* qs = P.qs + q;
+    uint32_t* cnts = P.counts + (size_t)q * P.B;
+    uint32_t active = __ldcg(&qs->active);
+    uint32_t size = 0;
+    if (active && __ldcg(&qs->aborted)) {
+      active = 0;
+      if (lane == 0) {
+        qs->active = 0;
+        qs->redist = 0;
+        qs->result = kInf;
+      }
+    }
+    if (active && !fatal) {
+      uint32_t cur = __ldcg(&qs->cur), head = __ldcg(&qs->head), tail = __ldcg(&qs->tail);
+      uint32_t redist = __ldcg(&qs->redist);
+      if (done_phase == kPhRelax) {
+        const uint32_t c = cur & P.Bmask;
+        const uint32_t cnt = min(__ldcg(cnts + c), P.cap);
+        if (cnt > tail) {  // the current bucket received entries: process it again
+          head = tail;
+          tail = cnt;
+        } else {           // current bucket finished: find the next non-empty one
+          uint32_t next = kInf;
+          for (uint32_t base = 1; base < P.B; base += 32) {
+            const uint32_t k = base + lane;
+            const bool ne = k < P.B && __ldcg(cnts + ((cur + k) & P.Bmask)) > 0u;
+            const unsigned b = __ballot_sync(FULL, ne);
+            if (b) {
+              next = cur + base + (uint32_t)(__ffs(b) - 1);
+              break;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) cnts[c] = 0u;
+          const uint32_t ovf_n = __ldcg(&qs->ovf_n), ovf_min = __ldcg(&qs->ovf_min);
+          if (ovf_n > 0 && ovf_min <= next) {
+            redist = 1;
+            if (lane == 0) {
+              qs->redist_min = next;
+              qs->ovf_n2 = 0;
+              qs->ovf_min2 = kInf;
+            }
+          } else if (next == kInf) {
+            active = 0;
+          } else {
+            cur = next;
+            head = 0;
+            tail = min(__ldcg(cnts + (next & P.Bmask)), P.cap);
+          }
+        }
+      } else if (done_phase == kPhRedistMin && redist) {
+        const uint32_t nc = __ldcg(&qs->redist_min);
+        if (nc == kInf) {  // every pile entry was out of date and the ring is empty
+          active = 0;
+          redist = 0;
+          if (lane == 0) qs->ovf_n = 0;
+        } else {
+          cur = nc;
+        }
+      } else if (done_phase == kPhRedistMove && redist) {
+        if (lane == 0) {
+          qs->ovf_sel = __ldcg(&qs->ovf_sel) ^ 1u;
+          qs->ovf_n = __ldcg(&qs->ovf_n2);
+          qs->ovf_min = __ldcg(&qs->ovf_min2);
+        }
+        redist = 0;
+        head = 0;
+        tail = min(__ldcg(cnts + (cur & P.Bmask)), P.cap);
+      }
+      const QDesc* qd = P.qd + q;
+      const uint32_t kind = __ldg(&qd->kind);
+      const uint32_t dst = __ldg(&qd->dst);
+      if (active && !redist && kind != kSSSP && !__ldcg(&qs->no_exit)) {
+        // Stop rule of Section 6.1 (PPSP): entering bucket i with i * Delta >= the best
+        // distance to the target found so far.
+        const uint32_t dt = __ldcg(P.dist + (size_t)q * P.n + dst);
+        if (dt != kInf && (unsigned long long)cur * __ldg(&qd->delta) >= dt) active = 0;
+      }
+      if (lane == 0) {
+        qs->cur = cur;
+        qs->head = head;
+        qs->tail = tail;
+        qs->redist = redist;
+        qs->active = active;
+        if (!active)
+          qs->result = dst < P.n ? __ldcg(P.dist + (size_t)q * P.n + dst) : 0u;
+        if (active) S.f_active = 1;
+        if (redist) S.f_redist = 1;
+      }
+      size = (active && !redist) ? tail - head : 0u;
+    }
+    if (lane == 0) S.pref[q] = size;
+  }
+  __syncthreads();
+  block_exscan(S.pref, P.nq, S.wtmp);
+  for (uint32_t q = tid; q <= P.nq; q += kBlock) P.fr_pref[q] = S.pref[q];
+  if (tid == 0) {
+    uint32_t next = kPhStop;
+    if (!fatal) {
+      if (done_phase == kPhRedistMin)
+        next = S.f_redist ? kPhRedistMove : (S.f_active ? kPhRelax : kPhStop);
+      else if (done_phase == kPhRedistMove)
+        next = S.f_active ? kPhRelax : kPhStop;
+      else
+        next = S.f_redist ? kPhRedistMin : (S.f_active ? kPhRelax : kPhStop);
+    }
+    if (next == kPhRelax) {
+      if (sy->rounds >= P.max_rounds) next = kPhStop;
+      else sy->rounds = sy->rounds + 1;
+    }
+    sy->phase = next;
+    sy->work = 0;
+    sy->total = S.pref[P.nq];
+    sy->any_active = S.f_active;
+    P.stats->v[kStRounds] += (next == kPhRelax) ? 1ull : 0ull;
+    if (done_phase == kPhRedistMove) P.stats->v[kStRedist] += 1ull;
+  }
+}
+
+// Grid-wide barrier with bounded waiting.  The last CTA to arrive runs decide() and then
+// releases the generation word; the others poll it with an acquire load and give up
+// (setting kErrTimeout) after spin_ns nanoseconds or as soon as a fatal error is posted.
+__device__ void grid_barrier(const Params& P, Smem& S, uint32_t& bar, uint32_t done_phase) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t a = atomicAdd(&P.sync->arrive, 1u);
+    S.last = (a == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (S.last) {
+    __threadfence();
+    decide(P, S, done_phase);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P.sync->arrive = 0;
+      __threadfence();
+      st_release(&P.sync->gen, bar + 1);
+    }
+  } else if (threadIdx.x == 0) {
+    const uint64_t t0 = gtimer();
+    uint32_t spins = 0;
+    while (ld_acquire(&P.sync->gen) <= bar) {
+      if (ld_relaxed(&P.sync->err) & kErrFatal) break;
+      if ((++spins & 31u) == 0 && gtimer() - t0 > P.spin_ns) {
+        atomicOr(&P.sync->err, kErrTimeout);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S.phase = ld_acquire(&P.sync->phase);
+    S.err = ld_relaxed(&P.sync->err);
+  }
+  __syncthreads();
+  ++bar;
+}
+
+// One round for all active queries: frontier pass over the global current buckets, then
+// the CTA-local fusion loop (Section 3.3).
+__device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uint32_t& fused) {
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t q = tid; q < P.nq; q += kBlock) {
+    S.cur[q] = __ldcg(&P.qs[q].cur);
+    S.head[q] = __ldcg(&P.qs[q].head);
+    S.pref[q] = __ldcg(P.fr_pref + q);
+  }
+  if (tid == 0) {
+    S.pref[P.nq] = __ldcg(P.fr_pref + P.nq);
+    S.binN[0] = 0;
+    S.binN[1] = 0;
+  }
+  __syncthreads();
+  const uint32_t total = S.pref[P.nq];
+  const bool fuse = P.T != 0;
+  for (;;) {
+    if (tid == 0) S.grab = atomicAdd(&P.sync->work, P.tile);
+    __syncthreads();
+    const uint32_t base = S.grab;
+    __syncthreads();
+    if (base >= total) break;
+    for (uint32_t k = tid; k < P.tile; k += kBlock) {
+      const uint32_t i = base + k;
+      const bool has = i < total;
+      uint32_t u = 0, g = 0, q = 0;
+      if (has) {
+        uint32_t lo = 0, hi = P.nq;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (S.pref[mid] <= i) lo = mid; else hi = mid;
+        }
+        q = lo;
+        const uint32_t pos = S.head[q] + (i - S.pref[q]);
+        const uint2 en =
+            __ldcg(P.ring + ((size_t)q * P.B + (S.cur[q] & P.Bmask)) * P.cap + pos);
+        u = en.x;
+        g = en.y;
+      }
+      expand_warp(P, S, B, 0, fuse, has, u, g, q, C);
+    }
+  }
+  if (!fuse) return;
+  int in = 0;
+  for (;;) {
+    __syncthreads();
+    const uint32_t nin = S.binN[in];
+    if (nin == 0) break;
+    const uint32_t cnt = min(nin, P.bin_cap);
+    const uint32_t lim = (cnt + 31u) & ~31u;
+    if (nin >= P.T) {
+      // Large local bucket: hand it to the global bucket for the next round.
+      for (uint32_t k = tid; k < lim; k += kBlock) {
+        const bool has = k < cnt;
+        uint2 en = make_uint2(0, 0);
+        uint32_t q = 0;
+        if (has) {
+          en = B.e[in][k];
+          q = B.q[in][k];
+        }
+        insert_warp(P, S, B, in ^ 1, has, false, en.x, en.y, has ? S.cur[q] : 0u, q, C);
+      }
+      __syncthreads();
+      if (tid == 0) S.binN[in] = 0;
+      break;
+    }
+    for (uint32_t k = tid; k < lim; k += kBlock) {
+      const bool has = k < cnt;
+      uint2 en = make_uint2(0, 0);
+      uint32_t q = 0;
+      if (has) {
+        en = B.e[in][k];
+        q = B.q[in][k];
+      }
+      expand_warp(P, S, B, in ^ 1, true, has, en.x, en.y, q, C);
+    }
+    __syncthreads();
+    if (tid == 0) S.binN[in] = 0;
+    in ^= 1;
+    ++fused;
+  }
+  __syncthreads();
+}
+
+// Overflow redistribution, step 1: the smallest bucket among live pile entries.
+__device__ void redist_min_phase(const Params& P) {
+  const uint32_t gtid = blockIdx.x * kBlock + threadIdx.x, gstride = gridDim.x * kBlock;
+  for (uint32_t q = 0; q < P.nq; ++q) {
+    QState* qs = P.qs + q;
+    if (!__ldcg(&qs->redist)) continue;
+    const uint32_t sel = __ldcg(&qs->ovf_sel);
+    const uint32_t n = min(__ldcg(&qs->ovf_n), P.ocap);
+    const QDesc* qd = P.qd + q;
+    const bool astar = __ldg(&qd->kind) == kASTAR;
+    const uint32_t delta = __ldg(&qd->delta);
+    const uint2* pile = P.ovf + ((size_t)q * 2 + sel) * P.ocap;
+    uint32_t best = kInf;
+    for (uint32_t i = gtid; i < n; i += gstride) {
+      const uint2 en = __ldcg(pile + i);
+      if (__ldcg(P.dist + (size_t)q * P.n + en.x) != en.y) continue;
+      const uint32_t h = astar ? heuristic(P, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
+      best = min(best, bucket_of(en.y, h, delta));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULL, best, o));
+    if ((threadIdx.x & 31) == 0 && best != kInf) atomicMin(&qs->redist_min, best);
+  }
+}
+
+// Overflow redistribution, step 2: live entries of the new ring window move into the
+// ring, the rest into the other pile.
+__device__ void redist_move_phase(const Params& P) {
+  const uint32_t gtid = blockIdx.x * kBlock + threadIdx.x, gstride = gridDim.x * kBlock;
+  for (uint32_t q = 0; q < P.nq; ++q) {
+    QState* qs = P.qs + q;
+    if (!__ldcg(&qs->redist)) continue;
+    const uint32_t sel = __ldcg(&qs->ovf_sel);
+    const uint32_t n = min(__ldcg(&qs->ovf_n), P.ocap);
+    const uint32_t cur = __ldcg(&qs->cur);
+    const QDesc* qd = P.qd + q;
+    const bool astar = __ldg(&qd->kind) == kASTAR;
+    const uint32_t delta = __ldg(&qd->delta);
+    const uint2* pile = P.ovf + ((size_t)q * 2 + sel) * P.ocap;
+    uint2* other = P.ovf + ((size_t)q * 2 + (sel ^ 1u)) * P.ocap;
+    for (uint32_t i = gtid; i < n; i += gstride) {
+      const uint2 en = __ldcg(pile + i);
+      if (__ldcg(P.dist + (size_t)q * P.n + en.x) != en.y) continue;
+      const uint32_t h = astar ? heuristic(P, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
+      const uint32_t key = bucket_of(en.y, h, delta);
+      bool to_pile = true;
+      if (key - cur < P.B) {
+        const uint32_t cid = q * P.B + (key & P.Bmask);
+        const uint32_t pos = atomicAdd(P.counts + cid, 1u);
+        if (pos < P.cap) {
+          P.ring[(size_t)cid * P.cap + pos] = en;
+          to_pile = false;
+        }
+      }
+      if (to_pile) {
+        const uint32_t pos = atomicAdd(&qs->ovf_n2, 1u);
+        atomicMin(&qs->ovf_min2, key);
+        if (pos < P.ocap) {
+          other[pos] = en;
+        } else {
+          qs->aborted = 1u;
+          atomicOr(&P.sync->err, kErrArena);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+
+extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
+  extern __shared__ __align__(16) unsigned char og_dyn_smem[];
+  __shared__ Smem S;
+  Bins B;
+  B.e[0] = reinterpret_cast<uint2*>(og_dyn_smem);
+  B.e[1] = B.e[0] + P.bin_cap;
+  B.q[0] = reinterpret_cast<uint16_t*>(B.e[1] + P.bin_cap);
+  B.q[1] = B.q[0] + P.bin_cap;
+  for (uint32_t q = threadIdx.x; q < P.nq; q += kBlock) S.delta[q] = __ldg(&P.qd[q].delta);
+  Cnt C = {0, 0, 0, 0, 0, 0, 0};
+  uint32_t fused = 0;
+  uint32_t bar = 0;
+  grid_barrier(P, S, bar, kPhPrologue);
+  for (;;) {
+    const uint32_t phase = S.phase;
+    if (phase == kPhStop || (S.err & kErrFatal)) break;
+    if (phase == kPhRelax) relax_phase(P, S, B, C, fused);
+    else if (phase == kPhRedistMin) redist_min_phase(P);
+    else if (phase == kPhRedistMove) redist_move_phase(P);
+    grid_barrier(P, S, bar, phase);
+  }
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t vals[7] = {C.items, C.stale, C.relax, C.improved, C.local, C.global, C.ovf};
+  const int idx[7] = {kStItems, kStStale, kStRelax, kStImproved, kStLocal, kStGlobal, kStOvf};
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const uint32_t s = warp_sum(vals[k]);
+    if (lane == 0 && s) atomicAdd(&P.stats->v[idx[k]], (unsigned long long)s);
+  }
+  if (threadIdx.x == 0 && fused) atomicAdd(&P.stats->v[kStFused], (unsigned long long)fused);
+}
+
+// dist[slot][*] = unreachable for the listed slots (blockIdx.y indexes the slot list).
+extern "C" __global__ void og_fill_kernel(uint32_t* dist, uint32_t n, const uint32_t* slots) {
+  const uint32_t q = slots ? slots[blockIdx.y] : blockIdx.y;
+  uint32_t* d = dist + (size_t)q * n;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // align to 16 bytes for vector stores
+  const uint32_t mis = (uint32_t)(((uintptr_t)d >> 2) & 3u);
+  const uint32_t headn = mis ? min(n, 4u - mis) : 0u;
+  if (i < headn) d[i] = kInf;
+  const uint32_t body = (n - headn) / 4u;
+  uint4* d4 = reinterpret_cast<uint4*>(d + headn);
+  for (size_t k = i; k < body; k += stride) d4[k] = make_uint4(kInf, kInf, kInf, kInf);
+  for (size_t k = headn + 4ull * body + i; k < n; k += stride) d[k] = kInf;
+}
+
+// Starts the listed queries: dist[src] = 0 and the start vertex in its first bucket
+// (Section 3.2 figure: Dist[startV] = 0 and the bucket structure holding startV).
+extern "C" __global__ void og_init_kernel(Params P, const uint32_t* slots, uint32_t nslots) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nslots) return;
+  const uint32_t q = slots ? slots[t] : t;
+  const QDesc d = P.qd[q];
+  P.dist[(size_t)q * P.n + d.src] = 0u;
+  const uint32_t h0 = d.kind == kASTAR ? heuristic(P, d.src, d.tx, d.ty) : 0u;
+  const uint32_t key0 = bucket_of(0u, h0, d.delta);
+  uint32_t* cnts = P.counts + (size_t)q * P.B;
+  for (uint32_t k = 0; k < P.B; ++k) cnts[k] = 0u;
+  cnts[key0 & P.Bmask] = 1u;
+  P.ring[((size_t)q * P.B + (key0 & P.Bmask)) * P.cap] = make_uint2(d.src, 0u);
+  QState s;
+  s.cur = key0;
+  s.head = 0;
+  s.tail = 1;
+  s.active = 1;
+  s.ovf_n = 0;
+  s.ovf_min = kInf;
+  s.ovf_sel = 0;
+  s.redist = 0;
+  s.ovf_n2 = 0;
+  s.ovf_min2 = kInf;
+  s.redist_min = kInf;
+  s.no_exit = 0;
+  s.result = kInf;
+  s.aborted = 0;
+  s.pad[0] = s.pad[1] = 0;
+  P.qs[q] = s;
+}
+
+// Graph upload helpers: interleave {neighbor, weight}, validate neighbors, weight range.
+extern "C" __global__ void og_interleave_kernel(const uint32_t* nbr, const uint32_t* w,
+                                                uint2* adj, size_t m, uint32_t n,
+                                                uint32_t* flags /* [0]=bad, [1]=min, [2]=max */) {
+  uint32_t bad = 0, mn = kInf, mx = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t v = nbr[i], x = w[i];
+    bad |= v >= n;
+    mn = min(mn, x);
+    mx = max(mx, x);
+    adj[i] = make_uint2(v, x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bad |= __shfl_xor_sync(FULL, bad, o);
+    mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+    mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(flags, 1u);
+    atomicMin(flags + 1, mn);
+    atomicMax(flags + 2, mx);
+  }
+}
+
+}  // namespace og
+
+namespace og {
+
+// Host-side launchers (the kernels above are only launched through these).
+cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st) {
+  void* args[] = {const_cast<Params*>(&P)};
+  return cudaLaunchCooperativeKernel((const void*)og_delta_kernel, dim3(grid), dim3(kBlock),
+                                     args, smem, st);
+}
+
+cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute((const void*)og_delta_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)og_delta_kernel,
+                                                       kBlock, smem);
+}
+
+cudaError_t launch_fill(uint32_t* dist, uint32_t n, const uint32_t* slots, uint32_t nslots,
+                        int sms, cudaStream_t st) {
+  if (nslots == 0) return cudaSuccess;
+  const uint32_t per = (n / 4 + 255) / 256;
+  uint32_t gx = per < 1 ? 1 : per;
+  const uint32_t cap = (uint32_t)sms * 8u;
+  if (gx > cap) gx = cap;
+  og_fill_kernel<<<dim3(gx, nslots), 256, 0, st>>>(dist, n, slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots, cudaStream_t st) {
+  if (nslots == 0) return cudaSuccess;
+  og_init_kernel<<<(nslots + 127) / 128, 128, 0, st>>>(P, slots, nslots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj, size_t m,
+                              uint32_t n, uint32_t* flags, int sms, cudaStream_t st) {
+  og_interleave_kernel<<<sms * 4, 256, 0, st>>>(nbr, w, adj, m, n, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace og

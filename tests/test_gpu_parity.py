@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit-exact.
+
+Distances are integers, so every comparison is exact equality.  Where several schedules
+are legal (Delta, fusion threshold, tile, ring size, CTAs per SM) they must all give the
+same distances (Section 3.3: fusion never reorders priorities; Section 2: coarsening only
+changes the schedule).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def og():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1911_07260_gb300 as og
+    from paper_1911_07260_gb300 import build
+    build.build()
+    torch.cuda.init()
+    return og
+
+
+@pytest.fixture(scope="module")
+def grid256(gg, og):
+    g = gg.grid(256, 256, 1, 1000, seed=1)
+    return g, og.Graph.from_csr(g)
+
+
+def _dev(n):
+    import torch
+    return torch.empty(n, dtype=torch.int32, device="cuda")
+
+
+def _np(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_grid256_delta1000_bit_exact(og, orc, grid256):
+    g, G = grid256
+    ref = orc.dijkstra(g, 0)
+    got = og.sssp_delta(G, 0, 1000)
+    np.testing.assert_array_equal(got, ref)
+    # device output buffer gives the same answer
+    d = _dev(g.n)
+    og.sssp_delta(G, 0, 1000, out=d)
+    np.testing.assert_array_equal(_np(d), ref)
+
+
+@pytest.mark.parametrize("delta", [1, 2, 7, 1000, 1 << 20, 1 << 31])
+@pytest.mark.parametrize("fusion", [0xFFFFFFFE, 1, 64, 0xFFFFFFFF])
+def test_schedule_sweep_identical(og, orc, grid256, delta, fusion):
+    g, G = grid256
+    src = 31337
+    ref = orc.dijkstra(g, src)
+    cfg = og.config(delta=delta, fusion_threshold=fusion)
+    got, _, st = og.query_run(G, og.Q_SSSP, src, cfg=cfg)
+    np.testing.assert_array_equal(got, ref)
+    assert st.rounds >= 1 and st.relax >= g.m // 2
+
+
+@pytest.mark.parametrize("tile,ring,bps", [(32, 2, 1), (256, 4, 2), (2048, 64, 0), (96, 2, 3)])
+def test_tile_ring_occupancy_sweep(og, orc, grid256, tile, ring, bps):
+    g, G = grid256
+    ref = orc.dijkstra(g, 65535)
+    cfg = og.config(delta=37, expand_tile=tile, ring_buckets=ring, blocks_per_sm=bps)
+    got, _, st = og.query_run(G, og.Q_SSSP, 65535, cfg=cfg)
+    np.testing.assert_array_equal(got, ref)
+    if ring == 2:
+        assert st.overflow_inserts > 0 and st.redistributions > 0
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_small_graphs(og, orc, gg, seed):
+    """Ragged shapes: zero weights, self loops, parallel edges, unreachable parts,
+    isolated vertices, a hub of high degree."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 3000))
+    m = int(rng.integers(0, 8 * n))
+    g = gg.random_graph(n, m, wlo=0, whi=int(rng.choice([2, 30, 1000, 100000])), seed=seed,
+                        symmetric=bool(seed % 3 == 0))
+    if seed % 5 == 0 and n > 10:  # add a hub with many out-edges
+        s = np.concatenate([np.repeat(np.arange(n), np.diff(g.offsets).astype(np.int64)),
+                            np.zeros(5 * n, np.int64)])
+        d = np.concatenate([g.nbr, rng.integers(0, n, 5 * n)])
+        w = np.concatenate([g.w, rng.integers(0, 50, 5 * n)])
+        g = gg.from_edges(n, s, d, w)
+    G = og.Graph.from_csr(g)
+    for src in {0, int(rng.integers(0, n)), n - 1}:
+        ref = orc.dijkstra(g, src)
+        delta = int(rng.choice([1, 3, 64, 5000]))
+        fusion = int(rng.choice([0xFFFFFFFE, 2, 128, 0xFFFFFFFF]))
+        got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=og.config(delta=delta,
+                                                                   fusion_threshold=fusion))
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_single_vertex_and_edgeless(og, orc, gg):
+    g = gg.from_edges(1, [], [], [])
+    G = og.Graph.from_csr(g)
+    assert og.sssp_delta(G, 0, 5).tolist() == [0]
+    g = gg.from_edges(7, [3], [3], [4])  # only a self loop
+    G = og.Graph.from_csr(g)
+    assert og.sssp_delta(G, 3, 1).tolist() == [INF] * 3 + [0] + [INF] * 3
+
+
+def test_wbfs_unit_weights_is_bfs(og, orc, gg):
+    g = gg.random_graph(5000, 20000, wlo=1, whi=2, seed=11, symmetric=True)
+    G = og.Graph.from_csr(g)
+    for src in (0, 4999):
+        np.testing.assert_array_equal(og.wbfs(G, src), orc.bfs(g, src))
+
+
+def test_wbfs_rmat_small_weights(og, orc, gg):
+    g = gg.rmat(14, 16, 0.57, 0.19, 0.19, 1, 24, seed=1)
+    G = og.Graph.from_csr(g)
+    for src in gg.sample_sources(g, 3, seed=2):
+        np.testing.assert_array_equal(og.wbfs(G, int(src)), orc.dijkstra(g, int(src)))
+
+
+def test_wbfs_rejects_zero_weight(og, gg):
+    g = gg.path_graph([1, 0, 2])
+    G = og.Graph.from_csr(g)
+    with pytest.raises(og.OgError) as e:
+        og.wbfs(G, 0)
+    assert e.value.code == og.E_INVALID
+
+
+def test_sssp_rmat_weights_up_to_2e16(og, orc, gg):
+    g = gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 1 << 16, seed=3)
+    G = og.Graph.from_csr(g)
+    for src in gg.sample_sources(g, 2, seed=2):
+        ref = orc.dijkstra(g, int(src))
+        for delta in (256, 4096, 65536):
+            np.testing.assert_array_equal(og.sssp_delta(G, int(src), delta), ref)
+
+
+@pytest.fixture(scope="module")
+def road300(gg, og):
+    g = gg.road(300, seed=1)
+    return g, og.Graph.from_csr(g)
+
+
+def test_ppsp_and_astar_match_oracle(og, orc, gg, road300):
+    g, G = road300
+    pairs = gg.sample_pairs_grid_steps(g, 25, 1, 400, seed=5)
+    for s, t in pairs.tolist():
+        ref = orc.ppsp(g, s, t)
+        for delta in (64, 1024, 16384):
+            assert og.ppsp(G, s, t, delta) == ref
+            assert og.astar(G, s, t, delta) == ref
+
+
+def test_ppsp_edge_cases(og, orc, gg, road300):
+    g, G = road300
+    assert og.ppsp(G, 5, 5, 100) == 0
+    assert og.astar(G, 5, 5, 100) == 0
+    # unreachable target
+    h = gg.from_edges(4, [0, 2], [1, 3], [5, 5])
+    H = og.Graph.from_csr(h)
+    assert og.ppsp(H, 0, 3, 4) == INF
+    with pytest.raises(og.OgError):
+        og.ppsp(H, 0, 99, 4)
+    with pytest.raises(og.OgError):  # A* needs coordinates
+        og.astar(H, 0, 1, 4)
+
+
+def test_astar_with_fractional_coordinates(og, orc, gg):
+    """Non-integral coordinates take the double-precision heuristic, reduced by one unit;
+    with Euclidean-consistent weights the result stays exact."""
+    rng = np.random.default_rng(3)
+    n = 400
+    xy = rng.uniform(0, 50, (n, 2)).astype(np.float32)
+    s, d = rng.integers(0, n, 3000), rng.integers(0, n, 3000)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    length = np.sqrt(((xy[s].astype(np.float64) - xy[d]) ** 2).sum(1))
+    w = np.ceil(100 * length).astype(np.uint32) + rng.integers(0, 30, s.size).astype(np.uint32)
+    g = gg.from_edges(n, np.concatenate([s, d]), np.concatenate([d, s]),
+                      np.concatenate([w, w]), xy=xy)
+    G = og.Graph.from_csr(g)
+    for src, dst in rng.integers(0, n, (20, 2)).tolist():
+        assert og.astar(G, src, dst, 200) == orc.ppsp(g, src, dst)
+
+
+def test_batch_equals_alone(og, orc, gg, road300):
+    g, G = road300
+    srcs = gg.sample_sources(g, 6, seed=9)
+    pairs = gg.sample_pairs_grid_steps(g, 10, 10, 300, seed=9)
+    queries = [(og.Q_SSSP, int(s), 0, 2048) for s in srcs]
+    queries += [(og.Q_PPSP, int(a), int(b), 1024) for a, b in pairs[:5]]
+    queries += [(og.Q_ASTAR, int(a), int(b), 512) for a, b in pairs[5:]]
+    queries += [(og.Q_WBFS, int(srcs[0]), 0, 0)]
+    out, d, st = og.batch_run(G, queries)
+    out = out.reshape(len(queries), g.n)
+    for i, (kind, s, t, delta) in enumerate(queries):
+        if kind == og.Q_SSSP:
+            np.testing.assert_array_equal(out[i], orc.dijkstra(g, s))
+            np.testing.assert_array_equal(out[i], og.sssp_delta(G, s, delta))
+        elif kind == og.Q_WBFS:
+            np.testing.assert_array_equal(out[i], orc.dijkstra(g, s))
+        else:
+            assert d[i] == orc.ppsp(g, s, t)
+    assert st.rounds > 0
+
+
+def test_batch_device_output(og, orc, gg, road300):
+    import torch
+    g, G = road300
+    srcs = [0, 100, 2000]
+    buf = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+    og.batch_run(G, [(og.Q_SSSP, s, 0, 0) for s in srcs], out=buf)
+    got = _np(buf).reshape(len(srcs), g.n)
+    for i, s in enumerate(srcs):
+        np.testing.assert_array_equal(got[i], orc.dijkstra(g, s))
+
+
+def test_arena_regrowth_keeps_results_exact(og, orc, grid256):
+    g, G = grid256
+    ref = orc.dijkstra(g, 123)
+    cfg = og.config(delta=50, ring_buckets=2, arena_entries=300)
+    got, _, st = og.query_run(G, og.Q_SSSP, 123, cfg=cfg)
+    np.testing.assert_array_equal(got, ref)
+    assert st.restarts >= 1
+
+
+def test_barrier_timeout_is_reported_and_context_survives(og, orc, grid256):
+    """A wait limit of 1 ns makes the grid barrier give up: the call returns
+    OG_E_TIMEOUT instead of hanging, and the next call still works."""
+    g, G = grid256
+    with pytest.raises(og.OgError) as e:
+        og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=1000, spin_limit_ns=1))
+    assert e.value.code == og.E_TIMEOUT
+    np.testing.assert_array_equal(og.sssp_delta(G, 0, 1000), orc.dijkstra(g, 0))
+
+
+def test_distance_saturation_reported(og, gg):
+    g = gg.path_graph([0xFFFFFFF0, 0x10, 0x10])
+    G = og.Graph.from_csr(g)
+    with pytest.raises(og.OgError) as e:
+        og.sssp_delta(G, 0, 1 << 20)
+    assert e.value.code == og.E_OVERFLOW
+
+
+def test_invalid_arguments(og, gg, grid256):
+    g, G = grid256
+    with pytest.raises(og.OgError) as e:
+        og.sssp_delta(G, g.n, 10)
+    assert e.value.code == og.E_INVALID
+    with pytest.raises(og.OgError):
+        og.Graph(np.array([0, 2], np.uint64), np.array([0, 5], np.uint32),
+                 np.array([1, 1], np.uint32))  # neighbor out of range
+    with pytest.raises(og.OgError):
+        og.Graph(np.array([0, 2, 1], np.uint64), np.array([0, 1], np.uint32),
+                 np.array([1, 1], np.uint32))  # offsets not monotone
+
+
+def test_fusion_cuts_rounds_on_road_graph(og, orc, road300):
+    """Section 6.4 (Table "Running times and number of rounds reductions with the bucket
+    fusion optimization"): fusion processes the same bucket without a global round;
+    the result is unchanged and the number of global rounds drops."""
+    g, G = road300
+    ref = orc.dijkstra(g, 0)
+    _, _, off = og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=2048, fusion_threshold=0xFFFFFFFE),
+                             out=np.empty(g.n, np.uint32))
+    got, _, on = og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=2048, fusion_threshold=2048))
+    np.testing.assert_array_equal(got, ref)
+    assert on.rounds * 3 < off.rounds, (on.rounds, off.rounds)
+    assert on.fused_iters > 0 and off.fused_iters == 0
