@@ -42,6 +42,8 @@ extern "C" {
 #define OG_E_TIMEOUT 5   /* a bounded device wait (grid barrier) gave up             */
 #define OG_E_BUSY 6      /* no free serving slot                                      */
 #define OG_E_ARENA 7     /* bucket arena exhausted even after regrowth                */
+#define OG_E_INTERNAL 8  /* an internal consistency check failed inside a kernel (the
+                            access was skipped; og_last_cuda_error has the details)   */
 
 /* Query kinds (Section 6.1). */
 #define OG_Q_SSSP 0      /* all distances from src                                    */
@@ -66,12 +68,23 @@ typedef struct og_config {
   uint32_t ring_buckets;     /* materialised buckets (power of two, <= 64); further
                                 buckets go to one overflow pile (Section 5.1's lazy
                                 queue idea of a few materialised buckets + overflow)   */
-  uint32_t reserved0;
+  uint32_t engine;           /* OG_ENGINE_ROUNDS or OG_ENGINE_ASYNC (0 = default: rounds) */
   uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
   uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
 } og_config;
 
 #define OG_FUSION_OFF 0xFFFFFFFEu
+
+/* Engines.  Both run the same eager Delta-stepping with bucket fusion and give the same
+ * distances.  ROUNDS (the default) follows the paper's round structure: every CTA fuses
+ * rounds of its local bucket with block-level synchronisation, and rounds are separated
+ * by a grid-wide barrier (rounds counts those barriers).  ASYNC replaces the grid barrier
+ * by a per-query completion count: each warp fuses its own local bucket, idle warps take
+ * over copied buckets, and a query moves to its next bucket the moment its current one
+ * has no outstanding entry (rounds counts those bucket transitions). */
+#define OG_ENGINE_DEFAULT 0u
+#define OG_ENGINE_ROUNDS 1u
+#define OG_ENGINE_ASYNC 2u
 
 /* Counters of one call (summed over its queries). */
 typedef struct og_stats {
@@ -87,7 +100,8 @@ typedef struct og_stats {
   uint64_t redistributions;  /* overflow-pile redistributions                          */
   uint64_t restarts;         /* arena regrowth restarts                                */
   uint64_t kernel_ns;        /* device time of the persistent kernel(s), CUDA events   */
-  uint64_t reserved[4];
+  uint64_t flushes;          /* local buckets copied to a global bucket (fusion limit) */
+  uint64_t reserved[3];
 } og_stats;
 
 typedef struct og_query {
@@ -171,14 +185,16 @@ int og_batch_run(og_graph* g, const og_query* q, uint32_t nq, const og_config* c
 /* ---- serving (continuous batching) -----------------------------------------------------
  * A server keeps the graph and up to max_slots queries resident.  og_server_submit
  * admits a PPSP / A* / SSSP query into a free slot (OG_E_BUSY if none).  og_server_step
- * advances every admitted query by up to max_rounds rounds in one persistent launch;
- * queries admitted between steps join the next launch.  og_server_poll returns finished
- * queries (tag and dist(src, dst)) and frees their slots.  Results do not depend on what
- * else is in flight.  max_slots = 0 sizes the slot count from free device memory. */
+ * runs one persistent launch of the barrier-free engine over every admitted query for at
+ * most budget_us microseconds (0 = until all admitted queries finish); a query that is
+ * not done keeps its state and continues in the next step, and queries admitted between
+ * steps join the next launch.  og_server_poll returns finished queries (tag and
+ * dist(src, dst)) and frees their slots.  Results do not depend on what else is in
+ * flight.  max_slots = 0 sizes the slot count from free device memory. */
 int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void* stream,
                      og_server** out);
 int og_server_submit(og_server* s, const og_query* q, uint64_t tag);
-int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active);
+int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active);
 int og_server_poll(og_server* s, uint64_t* tags, uint32_t* d_out, uint32_t cap,
                    uint32_t* n_done);
 int og_server_slots(const og_server* s, uint32_t* max_slots, uint32_t* n_free);

@@ -20,10 +20,11 @@ LIB_PATH = os.path.join(_PKG, "libog.so")
 HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "og.h")
 _lib = None
 
-OK, E_INVALID, E_OOM, E_CUDA, E_OVERFLOW, E_TIMEOUT, E_BUSY, E_ARENA = range(8)
+OK, E_INVALID, E_OOM, E_CUDA, E_OVERFLOW, E_TIMEOUT, E_BUSY, E_ARENA, E_INTERNAL = range(9)
 Q_SSSP, Q_PPSP, Q_ASTAR, Q_WBFS = 0, 1, 2, 3
 FUSION_OFF = 0xFFFFFFFE
 FUSION_UNBOUNDED = 0xFFFFFFFF
+ENGINE_DEFAULT, ENGINE_ROUNDS, ENGINE_ASYNC = 0, 1, 2
 UNREACHED = 0xFFFFFFFF
 
 
@@ -31,7 +32,7 @@ class OgError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         msg = f"{where}: {strerror(code)}"
-        if code == E_CUDA:
+        if code in (E_CUDA, E_INTERNAL, E_TIMEOUT):
             msg += f" ({last_cuda_error()})"
         super().__init__(msg)
 
@@ -39,7 +40,7 @@ class OgError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_uint32), ("fusion_threshold", ctypes.c_uint32),
                 ("expand_tile", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
-                ("ring_buckets", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("ring_buckets", ctypes.c_uint32), ("engine", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("arena_entries", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -50,10 +51,10 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("rounds", "fused_iters", "items", "stale", "relax", "improved",
                  "local_inserts", "global_inserts", "overflow_inserts", "redistributions",
-                 "restarts", "kernel_ns", "r0", "r1", "r2", "r3")]
+                 "restarts", "kernel_ns", "flushes", "r1", "r2", "r3")]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k not in ("r0", "r1", "r2", "r3")}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k not in ("r1", "r2", "r3")}
 
 
 class Query(ctypes.Structure):
@@ -313,9 +314,11 @@ class Server:
         _check(r, "og_server_submit")
         return True
 
-    def step(self, max_rounds: int = 0) -> int:
+    def step(self, budget_us: int = 0) -> int:
+        """One launch over the admitted queries, at most budget_us (0 = to completion);
+        returns how many are still running."""
         n = ctypes.c_uint32()
-        _check(lib().og_server_step(self._h, max_rounds, ctypes.byref(n)), "og_server_step")
+        _check(lib().og_server_step(self._h, budget_us, ctypes.byref(n)), "og_server_step")
         return n.value
 
     def poll(self, cap: int = 4096):

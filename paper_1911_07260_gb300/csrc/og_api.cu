@@ -27,6 +27,10 @@ cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots,
                         cudaStream_t st);
 cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj, size_t m,
                               uint32_t n, uint32_t* flags, int sms, cudaStream_t st);
+cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t st);
+cudaError_t async_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,
+                              cudaStream_t st);
 }  // namespace og
 
 using namespace og;
@@ -100,13 +104,21 @@ struct HBuf {
 
 // Device scratch of one launch configuration (grown on demand, reused across calls).
 struct Workspace {
-  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots;
-  HBuf h_qd, h_qs, h_sync, h_stats, h_slots;
+  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq;
+  HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // Barrier-free engine: ring positions must read "free" (all ones) before use.  Entries
+  // [0, clean_upto) of the ring are known free except the listed dirty ranges.
+  uint64_t clean_upto = 0;
+  std::vector<std::pair<uint64_t, uint64_t>> dirty;
+  void* ring_ptr = nullptr;
   void release() {
-    for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots})
+    for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq})
       b->release();
-    for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots}) b->release();
+    for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq}) b->release();
+    clean_upto = 0;
+    dirty.clear();
+    ring_ptr = nullptr;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     e0 = e1 = nullptr;
@@ -142,7 +154,7 @@ uint32_t pow2_ceil(uint64_t x) {
 }
 
 constexpr uint32_t kDefaultFusion = 1024;
-constexpr uint32_t kDefaultTile = 512;
+constexpr uint32_t kDefaultTile = 128;
 constexpr uint32_t kBinCap = 2048;
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 
@@ -162,6 +174,7 @@ struct og_graph {
   Workspace ws;
   int sms = 0;
   int occ = 0;
+  int occ_async = 0;
 };
 
 struct og_server {
@@ -206,6 +219,7 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.ring_buckets = pick32(u.ring_buckets, g->cfg.ring_buckets, 0);
   r.spin_limit_ns = pick64(u.spin_limit_ns, g->cfg.spin_limit_ns, kDefaultSpinNs);
   r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
+  r.engine = u.engine ? u.engine : g->cfg.engine;
   return r;
 }
 
@@ -239,9 +253,10 @@ struct RunOut {
   uint64_t restarts = 0;
 };
 
-// Runs up to kMaxQ queries in one persistent launch, regrowing the arena when a query
-// runs out of bucket space.  dist_dev: nq*n device words (query i at + i*n).
-int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
+// Round-synchronous engine: up to kMaxQ queries in one persistent launch, regrowing the
+// arena when a query runs out of bucket space.  dist_dev: nq*n device words (query i at
+// + i*n).
+int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
               uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
   const size_t smem = 2 * (size_t)kBinCap * (sizeof(uint2) + sizeof(uint16_t));
   TRY(occupancy(g, smem));
@@ -320,6 +335,8 @@ int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og
     CK(cudaEventRecord(ws.e0, st));
     CK(launch_delta(P, g->sms * bps, smem, st));
     CK(cudaEventRecord(ws.e1, st));
+    ws.clean_upto = 0;  // this engine leaves entries in the ring: none of it reads "free"
+    ws.dirty.clear();
     CK(cudaMemcpyAsync(ws.h_sync.p, ws.sync.p, sizeof(Sync), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ws.h_stats.p, ws.stats.p, sizeof(Stats), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ws.h_qs.p, ws.qs.p, sizeof(QState) * nq, cudaMemcpyDeviceToHost, st));
@@ -332,7 +349,10 @@ int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og
     const Sync* hy = ws.h_sync.as<Sync>();
     const QState* hq = ws.h_qs.as<QState>();
     ro->err |= hy->err & ~(uint32_t)kErrArena;
-    if (hy->err & kErrTimeout) return OG_E_TIMEOUT;
+    if (hy->err & kErrTimeout) {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "grid barrier wait gave up");
+      return OG_E_TIMEOUT;
+    }
     pending.clear();
     for (uint32_t i = 0; i < nq; ++i)
       if (hq[i].aborted) pending.push_back(i);
@@ -345,6 +365,185 @@ int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og
     ro->restarts++;
   }
   return OG_OK;
+}
+
+constexpr uint32_t kLocalQueue = 512;  // per-warp FIFO entries (barrier-free engine)
+
+int occupancy_async(og_graph* g, size_t smem) {
+  if (!g->occ_async) {
+    int dev = 0, b = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(async_occupancy(&b, smem));
+    if (b < 1) {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "persistent kernel does not fit on an SM");
+      return OG_E_CUDA;
+    }
+    g->occ_async = b;
+  }
+  return OG_OK;
+}
+
+// Makes ring entries [0, need) read "free" before a barrier-free launch: the part never
+// used since allocation, and the regions of queries that stopped with entries left.
+int clean_ring(Workspace& ws, uint64_t need, cudaStream_t st) {
+  if (ws.ring_ptr != ws.ring.p) {
+    ws.ring_ptr = ws.ring.p;
+    ws.clean_upto = 0;
+    ws.dirty.clear();
+  }
+  for (const auto& r : ws.dirty) {
+    const uint64_t lo = r.first, hi = std::min(r.second, ws.clean_upto);
+    if (hi > lo)
+      CK(cudaMemsetAsync(ws.ring.as<uint2>() + lo, 0xFF, sizeof(uint2) * (hi - lo), st));
+  }
+  ws.dirty.clear();
+  if (need > ws.clean_upto) {
+    CK(cudaMemsetAsync(ws.ring.as<uint2>() + ws.clean_upto, 0xFF,
+                       sizeof(uint2) * (need - ws.clean_upto), st));
+    ws.clean_upto = need;
+  }
+  return OG_OK;
+}
+
+AParams async_params(const og_graph* g, Workspace& ws, uint32_t* dist, uint32_t nq, uint32_t B,
+                     uint32_t cap, uint32_t ocap, const og_config& c, bool astar) {
+  AParams P{};
+  P.off = g->off;
+  P.adj = g->adj;
+  P.xy = g->xy;
+  P.n = g->n;
+  P.xy_integral = g->xy_integral ? 1u : 0u;
+  P.dist = dist;
+  P.qd = ws.qd.as<QDesc>();
+  P.aq = ws.aq.as<AQState>();
+  P.ring = ws.ring.as<uint2>();
+  P.counts = ws.counts.as<uint32_t>();
+  P.ovf = ws.ovf.as<uint2>();
+  P.sync = ws.sync.as<Sync>();
+  P.stats = ws.stats.as<Stats>();
+  P.nq = nq;
+  P.B = B;
+  P.Bmask = B - 1;
+  P.cap = cap;
+  P.ocap = ocap;
+  P.T = c.fusion_threshold == OG_FUSION_OFF ? 0u : c.fusion_threshold;
+  P.lq_cap = kLocalQueue;
+  P.has_astar = astar ? 1u : 0u;
+  P.spin_ns = c.spin_limit_ns;
+  P.budget_ns = 0;
+  return P;
+}
+
+// Barrier-free engine: up to kMaxQ queries in one launch; queries that ran out of bucket
+// space rerun with twice the arena.
+int run_chunk_async(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq,
+                    const og_config& c, uint32_t* dist_dev, uint32_t* d_out, Stats* acc,
+                    RunOut* ro, cudaStream_t st) {
+  const size_t smem = (size_t)kWarps * kLocalQueue * sizeof(uint2);
+  TRY(occupancy_async(g, smem));
+  uint32_t min_delta = 0xFFFFFFFFu;
+  bool astar = false;
+  for (uint32_t i = 0; i < nq; ++i) {
+    min_delta = std::min(min_delta, qd[i].delta);
+    astar |= qd[i].kind == kASTAR;
+  }
+  const uint32_t B = ring_size(g, c, min_delta);
+  uint64_t entries = c.arena_entries ? c.arena_entries
+                                     : std::max<uint64_t>(6ull * g->n, 1ull << 16);
+  TRY(ws.events());
+  TRY(ws.h_qd.ensure(sizeof(QDesc) * nq));
+  TRY(ws.h_aq.ensure(sizeof(AQState) * nq));
+  TRY(ws.h_sync.ensure(sizeof(Sync)));
+  TRY(ws.h_stats.ensure(sizeof(Stats)));
+  memcpy(ws.h_qd.p, qd, sizeof(QDesc) * nq);
+  std::vector<uint32_t> pending(nq);
+  for (uint32_t i = 0; i < nq; ++i) pending[i] = i;
+  for (int attempt = 0;; ++attempt) {
+    const uint64_t cap64 = std::max<uint64_t>(64, entries / 2 / B);
+    const uint64_t ocap64 = std::max<uint64_t>(64, entries / 4);
+    if (cap64 >= 0xFFFFFFF0ull || ocap64 >= 0xFFFFFFF0ull) return OG_E_ARENA;
+    const uint32_t cap = (uint32_t)cap64, ocap = (uint32_t)ocap64;
+    const uint32_t np = (uint32_t)pending.size();
+    const uint64_t ring_entries = (uint64_t)nq * B * cap;
+    TRY(ws.ring.ensure(sizeof(uint2) * ring_entries));
+    TRY(ws.counts.ensure(sizeof(uint32_t) * (size_t)nq * B));
+    TRY(ws.ovf.ensure(sizeof(uint2) * (size_t)nq * 2 * ocap));
+    TRY(ws.aq.ensure(sizeof(AQState) * nq));
+    TRY(ws.qd.ensure(sizeof(QDesc) * nq));
+    TRY(ws.sync.ensure(sizeof(Sync)));
+    TRY(ws.stats.ensure(sizeof(Stats)));
+    TRY(ws.slots.ensure(sizeof(uint32_t) * nq));
+    TRY(ws.h_slots.ensure(sizeof(uint32_t) * nq));
+    memcpy(ws.h_slots.p, pending.data(), sizeof(uint32_t) * np);
+    TRY(clean_ring(ws, ring_entries, st));
+    AParams P = async_params(g, ws, dist_dev, nq, B, cap, ocap, c, astar);
+    CK(cudaMemcpyAsync(ws.qd.p, ws.h_qd.p, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.slots.p, ws.h_slots.p, sizeof(uint32_t) * np,
+                       cudaMemcpyHostToDevice, st));
+    if (attempt == 0) CK(cudaMemsetAsync(ws.aq.p, 0, sizeof(AQState) * nq, st));
+    CK(cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), st));
+    CK(cudaMemsetAsync(ws.stats.p, 0, sizeof(Stats), st));
+    CK(launch_fill(dist_dev, g->n, ws.slots.as<uint32_t>(), np, g->sms, st));
+    CK(launch_async_init(P, ws.slots.as<uint32_t>(), np, st));
+    const int bps = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, g->occ_async)
+                                    : g->occ_async;
+    CK(cudaEventRecord(ws.e0, st));
+    CK(launch_async(P, g->sms * bps, smem, st));
+    CK(cudaEventRecord(ws.e1, st));
+    CK(cudaMemcpyAsync(ws.h_sync.p, ws.sync.p, sizeof(Sync), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_stats.p, ws.stats.p, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_aq.p, ws.aq.p, sizeof(AQState) * nq, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ws.e0, ws.e1));
+    const Stats* hs = ws.h_stats.as<Stats>();
+    for (int k = 0; k < 16; ++k) acc->v[k] += hs->v[k];
+    acc->v[15] += (unsigned long long)(ms * 1.0e6);
+    const Sync* hy = ws.h_sync.as<Sync>();
+    const AQState* ha = ws.h_aq.as<AQState>();
+    ro->err |= hy->err & ~(uint32_t)kErrArena;
+    if (hy->err & kErrBounds) {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "internal check %u failed (value %u, context %u)",
+               hy->bad_code, hy->bad_val, hy->bad_aux);
+      return OG_E_INTERNAL;
+    }
+    const uint64_t per_q = (uint64_t)B * cap;
+    for (uint32_t i = 0; i < nq; ++i)
+      if (ha[i].dirty || ha[i].mode != kMDone)
+        ws.dirty.emplace_back(i * per_q, (i + 1) * per_q);
+    if (hy->err & kErrTimeout) {
+      int len = snprintf(g_cuda_msg, sizeof(g_cuda_msg), "wait %u gave up;", hy->timeout_at);
+      for (uint32_t i = 0; i < nq && len < 400; ++i)
+        if (ha[i].mode != kMDone)
+          len += snprintf(g_cuda_msg + len, sizeof(g_cuda_msg) - len,
+                          " q%u mode %u cur %u work %u claim %u", i, ha[i].mode, ha[i].cur,
+                          ha[i].work, (uint32_t)ha[i].word);
+      return OG_E_TIMEOUT;
+    }
+    pending.clear();
+    for (uint32_t i = 0; i < nq; ++i) {
+      if (ha[i].aborted) {
+        pending.push_back(i);
+        continue;
+      }
+      acc->v[kStRounds] += ha[i].advances;
+      acc->v[kStRedist] += ha[i].redists;
+      if (d_out) d_out[i] = qd[i].kind == kSSSP ? 0u : ha[i].result;
+    }
+    if (pending.empty()) break;
+    if (attempt >= 6) return OG_E_ARENA;
+    entries *= 2;
+    ro->restarts++;
+  }
+  return OG_OK;
+}
+
+int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
+              uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
+  if (c.engine == OG_ENGINE_ASYNC)
+    return run_chunk_async(g, ws, qd, nq, c, dist_dev, d_out, acc, ro, st);
+  return run_chunk_rounds(g, ws, qd, nq, c, dist_dev, d_out, acc, ro, st);
 }
 
 void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
@@ -362,6 +561,7 @@ void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
   out->redistributions = s.v[kStRedist];
   out->restarts = restarts;
   out->kernel_ns = s.v[15];
+  out->flushes = s.v[kStFlush];
 }
 
 int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d) {
@@ -446,6 +646,7 @@ const char* og_strerror(int code) {
     case OG_E_TIMEOUT: return "bounded device wait timed out";
     case OG_E_BUSY: return "no free slot";
     case OG_E_ARENA: return "bucket arena exhausted";
+    case OG_E_INTERNAL: return "internal consistency check failed";
     default: return "unknown error";
   }
 }
@@ -645,7 +846,7 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
                                ? s->cfg.arena_entries
                                : std::max<uint64_t>((uint64_t)g->n / 2, 1ull << 20);
   const uint64_t per_slot = sizeof(uint32_t) * (uint64_t)g->n + sizeof(uint2) * entries +
-                            sizeof(QState) + sizeof(QDesc) + 64;
+                            sizeof(AQState) + sizeof(QDesc) + 64;
   uint32_t slots = max_slots;
   if (!slots) {
     size_t fr = 0, tot = 0;
@@ -671,19 +872,21 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   if (r == OG_OK) r = ws.ring.ensure(sizeof(uint2) * (size_t)slots * B * s->cap);
   if (r == OG_OK) r = ws.counts.ensure(sizeof(uint32_t) * (size_t)slots * B);
   if (r == OG_OK) r = ws.ovf.ensure(sizeof(uint2) * (size_t)slots * 2 * s->ocap);
-  if (r == OG_OK) r = ws.qs.ensure(sizeof(QState) * slots);
+  if (r == OG_OK) r = ws.aq.ensure(sizeof(AQState) * slots);
   if (r == OG_OK) r = ws.qd.ensure(sizeof(QDesc) * slots);
-  if (r == OG_OK) r = ws.pref.ensure(sizeof(uint32_t) * (slots + 1));
   if (r == OG_OK) r = ws.sync.ensure(sizeof(Sync));
   if (r == OG_OK) r = ws.stats.ensure(sizeof(Stats));
   if (r == OG_OK) r = ws.slots.ensure(sizeof(uint32_t) * slots);
   if (r == OG_OK) r = ws.h_qd.ensure(sizeof(QDesc) * slots);
-  if (r == OG_OK) r = ws.h_qs.ensure(sizeof(QState) * slots);
+  if (r == OG_OK) r = ws.h_aq.ensure(sizeof(AQState) * slots);
   if (r == OG_OK) r = ws.h_sync.ensure(sizeof(Sync));
   if (r == OG_OK) r = ws.h_slots.ensure(sizeof(uint32_t) * slots);
   if (r == OG_OK) r = ws.events();
-  if (r == OG_OK && cudaMemsetAsync(ws.qs.p, 0, sizeof(QState) * slots, s->stream) != cudaSuccess)
+  if (r == OG_OK && cudaMemsetAsync(ws.aq.p, 0, sizeof(AQState) * slots, s->stream) != cudaSuccess)
     r = OG_E_CUDA;
+  if (r == OG_OK && cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), s->stream) != cudaSuccess)
+    r = OG_E_CUDA;
+  if (r == OG_OK) r = clean_ring(ws, (uint64_t)slots * B * s->cap, s->stream);
   if (r == OG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = OG_E_CUDA;
   if (r != OG_OK) {
     og_server_free(s);
@@ -712,13 +915,14 @@ int og_server_submit(og_server* s, const og_query* q, uint64_t tag) {
   return OG_OK;
 }
 
-int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active) {
+// One launch of the barrier-free engine over all slots, bounded by budget_us.
+int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active) {
   if (!s) return OG_E_INVALID;
   og_graph* g = s->g;
   Workspace& ws = s->ws;
   cudaStream_t st = s->stream;
-  const size_t smem = 2 * (size_t)kBinCap * (sizeof(uint2) + sizeof(uint16_t));
-  TRY(occupancy(g, smem));
+  const size_t smem = (size_t)kWarps * kLocalQueue * sizeof(uint2);
+  TRY(occupancy_async(g, smem));
   bool astar = false;
   uint32_t running = 0;
   for (uint32_t i = 0; i < s->slots; ++i) {
@@ -729,32 +933,10 @@ int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active) {
   }
   if (n_active) *n_active = running;
   if (!running) return OG_OK;
-  Params P{};
-  P.off = g->off;
-  P.adj = g->adj;
-  P.xy = g->xy;
-  P.n = g->n;
-  P.xy_integral = g->xy_integral ? 1u : 0u;
-  P.dist = ws.dist.as<uint32_t>();
-  P.qd = ws.qd.as<QDesc>();
-  P.qs = ws.qs.as<QState>();
-  P.ring = ws.ring.as<uint2>();
-  P.counts = ws.counts.as<uint32_t>();
-  P.ovf = ws.ovf.as<uint2>();
-  P.fr_pref = ws.pref.as<uint32_t>();
-  P.sync = ws.sync.as<Sync>();
-  P.stats = ws.stats.as<Stats>();
-  P.nq = s->slots;
-  P.B = s->B;
-  P.Bmask = s->B - 1;
-  P.cap = s->cap;
-  P.ocap = s->ocap;
-  P.T = s->cfg.fusion_threshold == OG_FUSION_OFF ? 0u : s->cfg.fusion_threshold;
-  P.tile = std::max<uint32_t>(32, (s->cfg.expand_tile + 31) / 32 * 32);
-  P.bin_cap = kBinCap;
-  P.max_rounds = max_rounds ? max_rounds : 0xFFFFFFFFu;
-  P.has_astar = astar ? 1u : 0u;
-  P.spin_ns = s->cfg.spin_limit_ns;
+  TRY(clean_ring(ws, (uint64_t)s->slots * s->B * s->cap, st));
+  AParams P = async_params(g, ws, ws.dist.as<uint32_t>(), s->slots, s->B, s->cap, s->ocap,
+                           s->cfg, astar);
+  P.budget_ns = (unsigned long long)budget_us * 1000ull;
   const uint32_t np = (uint32_t)s->pending.size();
   if (np) {
     QDesc* hqd = ws.h_qd.as<QDesc>();
@@ -764,28 +946,36 @@ int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active) {
     CK(cudaMemcpyAsync(ws.slots.p, ws.h_slots.p, sizeof(uint32_t) * np,
                        cudaMemcpyHostToDevice, st));
     CK(launch_fill(P.dist, g->n, ws.slots.as<uint32_t>(), np, g->sms, st));
-    CK(launch_init(P, ws.slots.as<uint32_t>(), np, st));
+    CK(launch_async_init(P, ws.slots.as<uint32_t>(), np, st));
     for (uint32_t slot : s->pending) s->state[slot] = 2;
     s->pending.clear();
   }
-  CK(cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), st));
-  CK(cudaMemsetAsync(ws.stats.p, 0, sizeof(Stats), st));
-  const int bps = s->cfg.blocks_per_sm ? std::min<int>((int)s->cfg.blocks_per_sm, g->occ) : g->occ;
-  CK(launch_delta(P, g->sms * bps, smem, st));
+  CK(cudaMemsetAsync(&ws.sync.as<Sync>()->err, 0, sizeof(uint32_t), st));
+  const int bps = s->cfg.blocks_per_sm ? std::min<int>((int)s->cfg.blocks_per_sm, g->occ_async)
+                                       : g->occ_async;
+  CK(launch_async(P, g->sms * bps, smem, st));
   CK(cudaMemcpyAsync(ws.h_sync.p, ws.sync.p, sizeof(Sync), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(ws.h_qs.p, ws.qs.p, sizeof(QState) * s->slots, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ws.h_aq.p, ws.aq.p, sizeof(AQState) * s->slots, cudaMemcpyDeviceToHost,
+                     st));
   CK(cudaStreamSynchronize(st));
   const Sync* hy = ws.h_sync.as<Sync>();
+  if (hy->err & kErrBounds) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "internal check %u failed (value %u, context %u)",
+             hy->bad_code, hy->bad_val, hy->bad_aux);
+    return OG_E_INTERNAL;
+  }
   if (hy->err & kErrTimeout) return OG_E_TIMEOUT;
-  const QState* hq = ws.h_qs.as<QState>();
+  const AQState* ha = ws.h_aq.as<AQState>();
+  const uint64_t per_q = (uint64_t)s->B * s->cap;
   running = 0;
   for (uint32_t i = 0; i < s->slots; ++i) {
     if (s->state[i] != 2) continue;
-    if (hq[i].active) {
+    if (ha[i].mode != kMDone) {
       ++running;
       continue;
     }
-    if (hq[i].aborted) {
+    if (ha[i].dirty) ws.dirty.emplace_back(i * per_q, (i + 1) * per_q);
+    if (ha[i].aborted) {
       // Arena too small for this query: answer it alone with a growing arena.
       og_query q{s->hq[i].kind == kASTAR ? (uint32_t)OG_Q_ASTAR
                  : s->hq[i].kind == kPPSP ? (uint32_t)OG_Q_PPSP : (uint32_t)OG_Q_SSSP,
@@ -794,7 +984,7 @@ int og_server_step(og_server* s, uint32_t max_rounds, uint32_t* n_active) {
       TRY(run_queries(g, &q, 1, &s->cfg, nullptr, &d, nullptr, st));
       s->results[i] = d;
     } else {
-      s->results[i] = s->hq[i].kind == kSSSP ? 0u : hq[i].result;
+      s->results[i] = s->hq[i].kind == kSSSP ? 0u : ha[i].result;
     }
     s->state[i] = 3;
     s->done.push_back(i);
@@ -844,50 +1034,61 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
   for (uint32_t i = 0; i < nsample; ++i)
     qs[i] = og_query{kind, srcs[i], dsts ? dsts[i] : 0u, 0u};
   og_config base = resolve(g, nullptr);
-  // Times one candidate: a warm-up run, then the device time of a second run.
-  auto measure = [&](const og_config& c, double* ns) -> int {
+  base.engine = OG_ENGINE_ROUNDS;
+  // One candidate: a warm-up run, then the device time of a second run.  A candidate
+  // that fails (e.g. a wait limit reached by a pathological schedule) is skipped.
+  auto measure = [&](const og_config& c, double* ns) -> bool {
     og_stats st;
     for (int rep = 0; rep < 2; ++rep)
-      TRY(run_queries(g, qs.data(), nsample, &c, nullptr, nullptr, &st, nullptr));
+      if (run_queries(g, qs.data(), nsample, &c, nullptr, nullptr, &st, nullptr) != OG_OK)
+        return false;
     *ns = (double)st.kernel_ns;
-    return OG_OK;
+    return true;
   };
   og_config best = base;
-  double best_ns = 0;
-  TRY(measure(best, &best_ns));
+  double best_ns = 1e300;
+  if (!measure(best, &best_ns)) return OG_E_CUDA;
+  auto consider = [&](const og_config& c) {
+    double ns;
+    if (measure(c, &ns) && ns < best_ns) {
+      best_ns = ns;
+      best = c;
+    }
+  };
+  // Delta (Section 6.2: the best coarsening factor depends on the graph), with fusion on.
   if (kind != OG_Q_WBFS) {
     if (!delta_lo) delta_lo = std::max(1u, default_delta(g) / 64);
     if (!delta_hi) delta_hi = std::max(delta_lo, default_delta(g) * 8);
+    const og_config anchor = best;
     for (uint64_t d = pow2_ceil(delta_lo); d <= delta_hi; d *= 2) {
-      og_config c = best;
+      og_config c = anchor;
       c.delta = (uint32_t)d;
-      double ns;
-      TRY(measure(c, &ns));
-      if (ns < best_ns) { best_ns = ns; best = c; }
+      consider(c);
     }
   }
-  const uint32_t fusions[] = {OG_FUSION_OFF, 64, 256, 1024, 2048, 0xFFFFFFFFu};
-  for (uint32_t f : fusions) {
+  // Fusion threshold (Section 5.2, configBucketFusionThreshold), frontier tile, CTAs/SM.
+  for (uint32_t f : {OG_FUSION_OFF, 256u, 1024u, 2048u, 0xFFFFFFFFu}) {
     og_config c = best;
     c.fusion_threshold = f;
-    double ns;
-    TRY(measure(c, &ns));
-    if (ns < best_ns) { best_ns = ns; best = c; }
+    consider(c);
   }
-  const uint32_t tiles[] = {128, 256, 512, 1024, 2048};
-  for (uint32_t t : tiles) {
+  for (uint32_t t : {32u, 64u, 128u, 256u, 512u}) {
     og_config c = best;
     c.expand_tile = t;
-    double ns;
-    TRY(measure(c, &ns));
-    if (ns < best_ns) { best_ns = ns; best = c; }
+    consider(c);
   }
-  for (uint32_t b = 1; b <= (uint32_t)g->occ; ++b) {
+  for (uint32_t b = 1; b <= (uint32_t)std::max(1, g->occ); ++b) {
     og_config c = best;
     c.blocks_per_sm = b;
-    double ns;
-    TRY(measure(c, &ns));
-    if (ns < best_ns) { best_ns = ns; best = c; }
+    consider(c);
+  }
+  // The barrier-free engine with warp-sized local buckets.
+  for (uint32_t f : {48u, 64u, 128u}) {
+    og_config c = best;
+    c.engine = OG_ENGINE_ASYNC;
+    c.fusion_threshold = f;
+    c.blocks_per_sm = 0;
+    consider(c);
   }
   g->cfg = best;
   if (out) *out = best;

@@ -34,9 +34,9 @@ enum Phase : uint32_t {
   kPhPrologue = 4,   // kernel start: publish the frontier of the current state
 };
 
-enum ErrBits : uint32_t { kErrTimeout = 1, kErrArena = 2, kErrSat = 4 };
+enum ErrBits : uint32_t { kErrTimeout = 1, kErrArena = 2, kErrSat = 4, kErrBounds = 8 };
 // A timeout stops the launch; an exhausted arena only stops the query that hit it.
-constexpr uint32_t kErrFatal = kErrTimeout;
+constexpr uint32_t kErrFatal = kErrTimeout | kErrBounds;
 
 struct QDesc {
   uint32_t src, dst, delta, kind;
@@ -69,12 +69,18 @@ struct Sync {
   uint32_t total;        // frontier entries in this phase
   uint32_t rounds;       // rounds run in this launch
   uint32_t any_active;
-  uint32_t pad[8];
+  uint32_t active;       // barrier-free engine: queries not yet finished
+  uint32_t bad_code;     // first failed internal bounds check (0 = none)
+  uint32_t bad_val;      // the offending value
+  uint32_t bad_aux;      // context (query or position)
+  uint32_t progress;     // barrier-free engine: heartbeat of busy warps
+  uint32_t timeout_at;   // which bounded wait gave up (1 idle, 2 entry hand-off)
+  uint32_t pad[2];
 };
 
 enum StatIdx {
   kStRounds, kStFused, kStItems, kStStale, kStRelax, kStImproved, kStLocal, kStGlobal,
-  kStOvf, kStRedist, kStCount
+  kStOvf, kStRedist, kStFlush, kStCount
 };
 struct Stats { unsigned long long v[16]; };
 
@@ -103,6 +109,47 @@ struct Params {
   uint32_t max_rounds;    // stop (resumably) after this many rounds
   uint32_t has_astar;
   unsigned long long spin_ns;
+};
+
+// ---- barrier-free engine (og_async.cu) -----------------------------------------------
+enum AMode : uint32_t { kMRelax = 0, kMRedistMin = 1, kMRedistMove = 2, kMDone = 3 };
+
+struct AQState {
+  unsigned long long word;  // (epoch << 32) | next unclaimed position of the current task
+  uint32_t mode;            // AMode: relax the current bucket / redistribute the pile
+  uint32_t cur;             // current bucket
+  uint32_t work;            // outstanding entries of the current task
+  uint32_t limit;           // size of a redistribution task
+  uint32_t ovf_n, ovf_min, ovf_sel, ovf_n2;
+  uint32_t ovf_min2, redist_min, no_exit, result;
+  uint32_t aborted;         // arena exhausted: the query stopped early
+  uint32_t dirty;           // ring positions may still hold entries (early exit / abort)
+  uint32_t advances;        // bucket / task transitions
+  uint32_t redists;         // overflow-pile redistributions
+};
+
+struct AParams {
+  const uint32_t* off;
+  const uint2* adj;
+  const float2* xy;
+  uint32_t n;
+  uint32_t xy_integral;
+  uint32_t* dist;
+  const QDesc* qd;
+  AQState* aq;
+  uint2* ring;              // positions hold {v, d} packed in 64 bits, or all ones when free
+  uint32_t* counts;
+  uint2* ovf;
+  Sync* sync;
+  Stats* stats;
+  uint32_t nq;
+  uint32_t B, Bmask;
+  uint32_t cap, ocap;
+  uint32_t T;               // fusion threshold (0 = off)
+  uint32_t lq_cap;          // per-warp FIFO capacity (entries)
+  uint32_t has_astar;
+  unsigned long long spin_ns;
+  unsigned long long budget_ns;  // stop (resumably) after this long; 0 = run to the end
 };
 
 }  // namespace og

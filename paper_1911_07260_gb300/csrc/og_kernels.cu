@@ -16,62 +16,9 @@
 //   * between rounds a bounded grid barrier runs; the CTA that arrives last picks the
 //     next bucket of every query (the smallest non-empty one, scanned with a warp ballot)
 //     and applies the PPSP / A* stop rule before it releases the others.
-#include "og_internal.cuh"
+#include "og_device.cuh"
 
 namespace og {
-
-#define FULL 0xffffffffu
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-// A* heuristic floor(100 * Euclidean distance to the target).  Integral coordinates:
-// exact integer square root of 10000 * (dx^2 + dy^2) (double estimate, then corrected
-// so that s^2 <= N < (s+1)^2).  Otherwise a double evaluation minus one unit, which stays
-// below the exact value.
-__device__ __forceinline__ uint32_t heuristic(const Params& P, uint32_t v, float tx, float ty) {
-  const float2 p = __ldg(P.xy + v);
-  if (P.xy_integral) {
-    const long long dx = (long long)p.x - (long long)tx;
-    const long long dy = (long long)p.y - (long long)ty;
-    const unsigned long long N = 10000ull * (unsigned long long)(dx * dx + dy * dy);
-    unsigned long long s = (unsigned long long)sqrt((double)N);
-    while (s * s > N) --s;
-    while ((s + 1) * (s + 1) <= N) ++s;
-    return s >= kSat ? kSat - 1 : (uint32_t)s;
-  }
-  const double dx = (double)p.x - (double)tx, dy = (double)p.y - (double)ty;
-  const double d = floor(100.0 * sqrt(dx * dx + dy * dy)) - 1.0;
-  if (!(d > 0.0)) return 0u;
-  return d >= 4.0e9 ? 4000000000u : (uint32_t)d;
-}
-
-// Priority coarsening (Section 2): bucket = floor(priority / Delta); A* priority is g + h.
-__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t h, uint32_t delta) {
-  if (h == 0) return d / delta;
-  return (uint32_t)(((unsigned long long)d + h) / delta);
-}
 
 struct Smem {
   uint32_t cur[kMaxQ];     // current bucket per query
@@ -161,34 +108,49 @@ __device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins
   }
 }
 
-// Relaxes one edge per lane (ok lanes): nd = g + w (saturating), atomicMin on dist[v];
-// an improvement is inserted eagerly into bucket floor((nd + h) / Delta).
-__device__ __forceinline__ void relax_warp(const Params& P, Smem& S, const Bins& B, int out,
-                                           bool allow_local, bool ok, uint32_t e, uint32_t g,
-                                           uint32_t q, Cnt& C) {
-  bool ins = false;
-  uint32_t v = 0, nd = 0, key = 0;
-  if (ok) {
-    const uint2 ew = __ldg(P.adj + e);
-    v = ew.x;
-    const unsigned long long s = (unsigned long long)g + ew.y;
-    nd = s >= kSat ? kSat : (uint32_t)s;
-    if (s >= kSat) atomicOr(&P.sync->err, kErrSat);
-    C.relax++;
-    uint32_t h = 0;
-    if (P.has_astar) {
-      const QDesc* d = P.qd + q;
-      if (__ldg(&d->kind) == kASTAR) h = heuristic(P, v, __ldg(&d->tx), __ldg(&d->ty));
-    }
-    const uint32_t old = atomicMin(P.dist + (size_t)q * P.n + v, nd);
-    if (nd < old) {
-      ins = true;
-      C.improved++;
-      key = bucket_of(nd, h, S.delta[q]);
+// Relaxes up to K edges per lane: nd = g + w (saturating), atomicMin on dist[v]; an
+// improvement is inserted eagerly into bucket floor((nd + h) / Delta).  All K neighbor
+// loads are issued before any atomic and all K atomics before any insert, so a lane keeps
+// K independent memory operations in flight instead of paying one round trip per edge.
+template <int K>
+__device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins& B, int out,
+                                            bool allow_local, const bool (&ok)[K],
+                                            const uint32_t (&e)[K], const uint32_t (&g)[K],
+                                            const uint32_t (&q)[K], Cnt& C) {
+  uint2 ew[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) ew[k] = ok[k] ? __ldg(P.adj + e[k]) : make_uint2(0u, 0u);
+  uint32_t h[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    h[k] = 0;
+    if (P.has_astar && ok[k]) {
+      const QDesc* d = P.qd + q[k];
+      if (__ldg(&d->kind) == kASTAR) h[k] = heuristic(P.xy, P.xy_integral, ew[k].x, __ldg(&d->tx), __ldg(&d->ty));
     }
   }
-  insert_warp(P, S, B, out, ins, allow_local, v, nd, key, q, C);
+  uint32_t nd[K], old[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const unsigned long long s = (unsigned long long)g[k] + ew[k].y;
+    nd[k] = s >= kSat ? kSat : (uint32_t)s;
+    if (ok[k] && s >= kSat) atomicOr(&P.sync->err, kErrSat);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    old[k] = ok[k] ? atomicMin(P.dist + (size_t)q[k] * P.n + ew[k].x, nd[k]) : 0u;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool ins = ok[k] && nd[k] < old[k];
+    C.relax += ok[k] ? 1u : 0u;
+    C.improved += ins ? 1u : 0u;
+    const uint32_t key = ins ? bucket_of(nd[k], h[k], S.delta[q[k]]) : 0u;
+    insert_warp(P, S, B, out, ins, allow_local, ew[k].x, nd[k], key, q[k], C);
+  }
 }
+
+constexpr int kLightBatch = 4;  // light-edge groups of 32 relaxed per batch
+constexpr int kHeavyBatch = 4;  // groups of 32 edges of one heavy vertex per batch
 
 // Expands the bucket entries held by a warp (one per lane with has): drops entries whose
 // vertex has a smaller distance by now (a newer entry exists), then relaxes all out-edges.
@@ -219,8 +181,18 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
     hm &= hm - 1;
     const uint32_t hb = __shfl_sync(FULL, beg, l), he = __shfl_sync(FULL, end, l);
     const uint32_t hg = __shfl_sync(FULL, g, l), hq = __shfl_sync(FULL, q, l);
-    for (uint32_t e0 = hb; e0 < he; e0 += 32)
-      relax_warp(P, S, B, out, allow_local, e0 + lane < he, e0 + lane, hg, hq, C);
+    for (uint32_t e0 = hb; e0 < he; e0 += 32 * kHeavyBatch) {
+      bool ok[kHeavyBatch];
+      uint32_t ee[kHeavyBatch], gg[kHeavyBatch], qq[kHeavyBatch];
+#pragma unroll
+      for (int k = 0; k < kHeavyBatch; ++k) {
+        ee[k] = e0 + 32u * k + lane;
+        ok[k] = ee[k] < he;
+        gg[k] = hg;
+        qq[k] = hq;
+      }
+      relax_batch<kHeavyBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
+    }
   }
   const uint32_t ld = heavy ? 0u : deg;
   uint32_t incl = ld;
@@ -231,17 +203,25 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
   }
   const uint32_t total = __shfl_sync(FULL, incl, 31);
   const uint32_t excl = incl - ld;
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t idx = base + lane;
-    uint32_t pos = 0;  // owner lane: number of lanes whose inclusive sum is <= idx
+  for (uint32_t base = 0; base < total; base += 32 * kLightBatch) {
+    bool ok[kLightBatch];
+    uint32_t ee[kLightBatch], gg[kLightBatch], qq[kLightBatch];
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      const uint32_t x = __shfl_sync(FULL, incl, pos + s - 1);
-      if (x <= idx) pos += s;
+    for (int k = 0; k < kLightBatch; ++k) {
+      const uint32_t idx = base + 32u * k + lane;
+      uint32_t pos = 0;  // owner lane: number of lanes whose inclusive sum is <= idx
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t x = __shfl_sync(FULL, incl, pos + s - 1);
+        if (x <= idx) pos += s;
+      }
+      const uint32_t ob = __shfl_sync(FULL, beg, pos), oe = __shfl_sync(FULL, excl, pos);
+      gg[k] = __shfl_sync(FULL, g, pos);
+      qq[k] = __shfl_sync(FULL, q, pos);
+      ok[k] = idx < total;
+      ee[k] = ob + (idx - oe);
     }
-    const uint32_t ob = __shfl_sync(FULL, beg, pos), oe = __shfl_sync(FULL, excl, pos);
-    const uint32_t og = __shfl_sync(FULL, g, pos), oq = __shfl_sync(FULL, q, pos);
-    relax_warp(P, S, B, out, allow_local, idx < total, ob + (idx - oe), og, oq, C);
+    relax_batch<kLightBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
   }
 }
 
@@ -553,7 +533,7 @@ __device__ void redist_min_phase(const Params& P) {
     for (uint32_t i = gtid; i < n; i += gstride) {
       const uint2 en = __ldcg(pile + i);
       if (__ldcg(P.dist + (size_t)q * P.n + en.x) != en.y) continue;
-      const uint32_t h = astar ? heuristic(P, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
+      const uint32_t h = astar ? heuristic(P.xy, P.xy_integral, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
       best = min(best, bucket_of(en.y, h, delta));
     }
 #pragma unroll
@@ -580,7 +560,7 @@ __device__ void redist_move_phase(const Params& P) {
     for (uint32_t i = gtid; i < n; i += gstride) {
       const uint2 en = __ldcg(pile + i);
       if (__ldcg(P.dist + (size_t)q * P.n + en.x) != en.y) continue;
-      const uint32_t h = astar ? heuristic(P, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
+      const uint32_t h = astar ? heuristic(P.xy, P.xy_integral, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
       const uint32_t key = bucket_of(en.y, h, delta);
       bool to_pile = true;
       if (key - cur < P.B) {
@@ -603,12 +583,6 @@ __device__ void redist_move_phase(const Params& P) {
       }
     }
   }
-}
-
-__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-  return x;
 }
 
 extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
@@ -667,7 +641,7 @@ extern "C" __global__ void og_init_kernel(Params P, const uint32_t* slots, uint3
   const uint32_t q = slots ? slots[t] : t;
   const QDesc d = P.qd[q];
   P.dist[(size_t)q * P.n + d.src] = 0u;
-  const uint32_t h0 = d.kind == kASTAR ? heuristic(P, d.src, d.tx, d.ty) : 0u;
+  const uint32_t h0 = d.kind == kASTAR ? heuristic(P.xy, P.xy_integral, d.src, d.tx, d.ty) : 0u;
   const uint32_t key0 = bucket_of(0u, h0, d.delta);
   uint32_t* cnts = P.counts + (size_t)q * P.B;
   for (uint32_t k = 0; k < P.B; ++k) cnts[k] = 0u;

@@ -50,23 +50,26 @@ def test_grid256_delta1000_bit_exact(og, orc, grid256):
     np.testing.assert_array_equal(_np(d), ref)
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("delta", [1, 2, 7, 1000, 1 << 20, 1 << 31])
 @pytest.mark.parametrize("fusion", [0xFFFFFFFE, 1, 64, 0xFFFFFFFF])
-def test_schedule_sweep_identical(og, orc, grid256, delta, fusion):
+def test_schedule_sweep_identical(og, orc, grid256, delta, fusion, engine):
     g, G = grid256
     src = 31337
     ref = orc.dijkstra(g, src)
-    cfg = og.config(delta=delta, fusion_threshold=fusion)
+    cfg = og.config(delta=delta, fusion_threshold=fusion, engine=engine)
     got, _, st = og.query_run(G, og.Q_SSSP, src, cfg=cfg)
     np.testing.assert_array_equal(got, ref)
     assert st.rounds >= 1 and st.relax >= g.m // 2
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("tile,ring,bps", [(32, 2, 1), (256, 4, 2), (2048, 64, 0), (96, 2, 3)])
-def test_tile_ring_occupancy_sweep(og, orc, grid256, tile, ring, bps):
+def test_tile_ring_occupancy_sweep(og, orc, grid256, tile, ring, bps, engine):
     g, G = grid256
     ref = orc.dijkstra(g, 65535)
-    cfg = og.config(delta=37, expand_tile=tile, ring_buckets=ring, blocks_per_sm=bps)
+    cfg = og.config(delta=37, expand_tile=tile, ring_buckets=ring, blocks_per_sm=bps,
+                    engine=engine)
     got, _, st = og.query_run(G, og.Q_SSSP, 65535, cfg=cfg)
     np.testing.assert_array_equal(got, ref)
     if ring == 2:
@@ -93,9 +96,10 @@ def test_random_small_graphs(og, orc, gg, seed):
         ref = orc.dijkstra(g, src)
         delta = int(rng.choice([1, 3, 64, 5000]))
         fusion = int(rng.choice([0xFFFFFFFE, 2, 128, 0xFFFFFFFF]))
-        got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=og.config(delta=delta,
-                                                                   fusion_threshold=fusion))
-        np.testing.assert_array_equal(got, ref)
+        for engine in (1, 2):
+            got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=og.config(
+                delta=delta, fusion_threshold=fusion, engine=engine))
+            np.testing.assert_array_equal(got, ref)
 
 
 def test_single_vertex_and_edgeless(og, orc, gg):
@@ -218,21 +222,25 @@ def test_batch_device_output(og, orc, gg, road300):
         np.testing.assert_array_equal(got[i], orc.dijkstra(g, s))
 
 
-def test_arena_regrowth_keeps_results_exact(og, orc, grid256):
+@pytest.mark.parametrize("engine", [1, 2])
+def test_arena_regrowth_keeps_results_exact(og, orc, grid256, engine):
     g, G = grid256
     ref = orc.dijkstra(g, 123)
-    cfg = og.config(delta=50, ring_buckets=2, arena_entries=300)
+    cfg = og.config(delta=50, ring_buckets=2, arena_entries=300, engine=engine)
     got, _, st = og.query_run(G, og.Q_SSSP, 123, cfg=cfg)
     np.testing.assert_array_equal(got, ref)
     assert st.restarts >= 1
 
 
-def test_barrier_timeout_is_reported_and_context_survives(og, orc, grid256):
-    """A wait limit of 1 ns makes the grid barrier give up: the call returns
+@pytest.mark.parametrize("engine", [1, 2])
+def test_barrier_timeout_is_reported_and_context_survives(og, orc, grid256, engine):
+    """A wait limit of 1 ns makes the bounded device waits give up (the grid barrier of
+    the round engine, the idle wait of the barrier-free engine): the call returns
     OG_E_TIMEOUT instead of hanging, and the next call still works."""
     g, G = grid256
     with pytest.raises(og.OgError) as e:
-        og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=1000, spin_limit_ns=1))
+        og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=1000, spin_limit_ns=1,
+                                                    engine=engine))
     assert e.value.code == og.E_TIMEOUT
     np.testing.assert_array_equal(og.sssp_delta(G, 0, 1000), orc.dijkstra(g, 0))
 
@@ -264,9 +272,36 @@ def test_fusion_cuts_rounds_on_road_graph(og, orc, road300):
     the result is unchanged and the number of global rounds drops."""
     g, G = road300
     ref = orc.dijkstra(g, 0)
-    _, _, off = og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=2048, fusion_threshold=0xFFFFFFFE),
-                             out=np.empty(g.n, np.uint32))
-    got, _, on = og.query_run(G, og.Q_SSSP, 0, cfg=og.config(delta=2048, fusion_threshold=2048))
+    rounds = dict(delta=2048, engine=og.ENGINE_ROUNDS)
+    _, _, off = og.query_run(G, og.Q_SSSP, 0, cfg=og.config(fusion_threshold=0xFFFFFFFE, **rounds))
+    got, _, on = og.query_run(G, og.Q_SSSP, 0, cfg=og.config(fusion_threshold=2048, **rounds))
     np.testing.assert_array_equal(got, ref)
     assert on.rounds * 3 < off.rounds, (on.rounds, off.rounds)
     assert on.fused_iters > 0 and off.fused_iters == 0
+
+
+def test_async_engine_fusion_keeps_work_local(og, orc, road300):
+    """Barrier-free engine: with fusion most inserts of the current bucket stay in the
+    warp's local bucket; without it every insert goes through a global bucket."""
+    g, G = road300
+    ref = orc.dijkstra(g, 7)
+    asy = dict(delta=2048, engine=og.ENGINE_ASYNC)
+    got_off, _, off = og.query_run(G, og.Q_SSSP, 7, cfg=og.config(fusion_threshold=0xFFFFFFFE,
+                                                                 **asy))
+    got_on, _, on = og.query_run(G, og.Q_SSSP, 7, cfg=og.config(fusion_threshold=256, **asy))
+    np.testing.assert_array_equal(got_off, ref)
+    np.testing.assert_array_equal(got_on, ref)
+    assert off.local_inserts == 0 and off.global_inserts >= g.n - 1
+    assert on.local_inserts > 4 * on.global_inserts
+    assert on.rounds == off.rounds  # one transition per non-empty bucket either way
+
+
+def test_ppsp_dirty_ring_reuse(og, orc, gg, road300):
+    """Early-exit queries leave entries behind; later calls on the same graph (same and
+    different ring layouts) must still be exact."""
+    g, G = road300
+    pairs = gg.sample_pairs_grid_steps(g, 12, 5, 60, seed=21)
+    for s, t in pairs.tolist():
+        assert og.ppsp(G, s, t, 256) == orc.ppsp(g, s, t)
+        np.testing.assert_array_equal(og.sssp_delta(G, s, 256), orc.dijkstra(g, s))
+        np.testing.assert_array_equal(og.sssp_delta(G, t, 16), orc.dijkstra(g, t))
