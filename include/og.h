@@ -208,6 +208,30 @@ void og_server_free(og_server* s);
 int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t* dsts,
                 uint32_t nsample, uint32_t delta_lo, uint32_t delta_hi, og_config* out);
 
+/* ---- allocation-free variant -----------------------------------------------------------
+ * og_sssp_delta_noalloc: the same Delta-stepping SSSP as og_sssp_delta for callers that
+ * cannot allocate device memory -- code inside a host application whose allocator has
+ * already claimed the GPU's memory, code on a path where cudaMalloc's implicit device
+ * synchronisation is not acceptable, code that must not meet an out-of-memory error
+ * after start-up.  It calls no cudaMalloc, cudaFree or other allocating routine.  The
+ * paper has no counterpart; this is a deployment variant.
+ *   offsets: device uint32[n+1]; edges: device uint32[2m] holding (neighbor, weight)
+ *   pairs, the out-edges of u at pairs offsets[u] .. offsets[u+1]-1; dist_out: device
+ *   uint32[n], receives every distance from src (0xFFFFFFFF = unreachable).  All three
+ *   stay owned by the caller.
+ *   Scratch: a 64 MiB static device array inside libog.so, reserved on every GPU that
+ *   loads the library until the process exits.  n above 2^20 (1,048,576) vertices is
+ *   rejected with OG_E_INVALID; a run whose buckets outgrow the array returns OG_E_ARENA
+ *   (it never grows).
+ *   The first call on a device looks up the array's device address (set-up, once per
+ *   device); make that first call before any stream capture.  Every call shares the
+ *   array and clears its state words first, so calls that overlap on the GPU (other
+ *   streams, other host threads) race: serialise them.  Synchronises stream before
+ *   returning, like og_sssp_delta. */
+int og_sssp_delta_noalloc(const uint32_t* offsets, const uint32_t* edges, uint32_t n,
+                          uint64_t m, uint32_t src, uint32_t delta, uint32_t* dist_out,
+                          void* stream);
+
 /* ---- diagnostics ----------------------------------------------------------------------- */
 const char* og_strerror(int code);
 const char* og_last_cuda_error(void);

@@ -96,6 +96,7 @@ def lib():
             "og_strerror": (ctypes.c_char_p, [i32]),
             "og_last_cuda_error": (ctypes.c_char_p, []),
             "og_version": (i32, []),
+            "og_sssp_delta_noalloc": (i32, [vp, vp, u32, u64, u32, u32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -348,6 +349,16 @@ def autotune(g: Graph, kind: int, srcs, dsts=None, delta_lo: int = 0, delta_hi: 
     _check(lib().og_autotune(g.handle, kind, srcs.ctypes.data, None if dd is None else dd.ctypes.data,
                              srcs.shape[0], delta_lo, delta_hi, ctypes.byref(c)), "og_autotune")
     return c
+
+
+def sssp_delta_noalloc(offsets, edges, n: int, m: int, src: int, delta: int, out,
+                       stream=None):
+    """Allocation-free SSSP: offsets (device uint32[n+1]), edges (device uint32[2m],
+    interleaved neighbor/weight pairs) and out (device uint32[n]) are the caller's; the
+    library's scratch is a fixed static device array (graphs of up to 2^20 vertices)."""
+    _check(lib().og_sssp_delta_noalloc(_ptr(offsets), _ptr(edges), n, m, src, delta, _ptr(out),
+                                       _stream(stream)), "og_sssp_delta_noalloc")
+    return out
 
 
 def version() -> int:

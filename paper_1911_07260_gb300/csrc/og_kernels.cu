@@ -735,3 +735,143 @@ cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj
 }
 
 }  // namespace og
+
+// ---- allocation-free entry point ----------------------------------------------------------
+// og_sssp_delta_noalloc runs the same round-synchronous kernel as og_sssp_delta, but its
+// scratch (query cursor, barrier words, counters, bucket ring and overflow pile) lives in
+// the fixed device array below instead of memory the library allocates.  It serves
+// callers that cannot call cudaMalloc: code inside a host application whose allocator has
+// already claimed the device memory, code on a path where cudaMalloc's implicit device
+// synchronisation is not acceptable, and code that must not meet an out-of-memory error
+// after start-up.  The array is reserved on every GPU that loads the library, for the
+// life of the process.
+#include <mutex>
+
+#include "og.h"
+
+namespace og {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;           // scratch array size (64 MiB)
+constexpr uint32_t kNoAllocMaxN = 1u << 20;             // largest graph accepted
+constexpr size_t kNoAllocHeader = 4096;                 // state words before the arena
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char og_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+int g_noalloc_occ[kNoAllocMaxDevices] = {};
+int g_noalloc_sms[kNoAllocMaxDevices] = {};
+}  // namespace
+
+}  // namespace og
+
+extern "C" int og_sssp_delta_noalloc(const uint32_t* offsets, const uint32_t* edges, uint32_t n,
+                                     uint64_t m, uint32_t src, uint32_t delta,
+                                     uint32_t* dist_out, void* stream) {
+  using namespace og;
+  if (!offsets || !dist_out || (m && !edges) || n == 0 || src >= n || delta == 0)
+    return OG_E_INVALID;
+  if (n > kNoAllocMaxN || m >= 0xFFFFFFFFull) return OG_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return OG_E_CUDA;
+  }
+  const size_t smem = 2 * (size_t)2048 * (sizeof(uint2) + sizeof(uint16_t));
+  void* base = nullptr;
+  {
+    // Set-up, once per device with that device current: the device address of the array
+    // (host code only ever sees a host-side stand-in for the symbol).
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, og_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return OG_E_CUDA;
+      }
+      int occ = 0, sms = 0;
+      if (delta_occupancy(&occ, smem) != cudaSuccess || occ < 1 ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return OG_E_CUDA;
+      }
+      g_noalloc_occ[dev] = occ;
+      g_noalloc_sms[dev] = sms;
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  unsigned char* b = static_cast<unsigned char*>(base);
+  // Header: Sync | Stats | QDesc | QState | frontier prefix | ring counters.
+  Sync* sync = reinterpret_cast<Sync*>(b);
+  Stats* stats = reinterpret_cast<Stats*>(b + 256);
+  QDesc* qd = reinterpret_cast<QDesc*>(b + 512);
+  QState* qs = reinterpret_cast<QState*>(b + 768);
+  uint32_t* pref = reinterpret_cast<uint32_t*>(b + 1024);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(b + 2048);
+  uint32_t max_w = 0xFFFFFFFFu;  // unknown without a pass over the edges: widest ring
+  uint32_t B = kMaxRing;
+  if (delta >= max_w / 2) B = 2;
+  const uint64_t arena = (kNoAllocBytes - kNoAllocHeader) / sizeof(uint2);
+  const uint32_t cap = (uint32_t)(arena / 2 / B);
+  const uint32_t ocap = (uint32_t)(arena / 4);
+  uint2* ring = reinterpret_cast<uint2*>(b + kNoAllocHeader);
+  uint2* ovf = ring + (size_t)B * cap;
+
+  QDesc hq;
+  memset(&hq, 0, sizeof(hq));
+  hq.src = src;
+  hq.dst = kNone;
+  hq.delta = delta;
+  hq.kind = kSSSP;
+  Params P{};
+  P.off = offsets;
+  P.adj = reinterpret_cast<const uint2*>(edges);
+  P.xy = nullptr;
+  P.n = n;
+  P.dist = dist_out;
+  P.qd = qd;
+  P.qs = qs;
+  P.ring = ring;
+  P.counts = counts;
+  P.ovf = ovf;
+  P.fr_pref = pref;
+  P.sync = sync;
+  P.stats = stats;
+  P.nq = 1;
+  P.B = B;
+  P.Bmask = B - 1;
+  P.cap = cap;
+  P.ocap = ocap;
+  P.T = 1024;
+  P.tile = 128;
+  P.bin_cap = 2048;
+  P.max_rounds = 0xFFFFFFFFu;
+  P.has_astar = 0;
+  P.spin_ns = 2000000000ull;
+  // Calls share the array: the state words start from zero on every call (two calls
+  // that overlap on the GPU would race on it).
+  if (cudaMemsetAsync(b, 0, kNoAllocHeader, st) != cudaSuccess ||
+      cudaMemcpyAsync(qd, &hq, sizeof(hq), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      launch_fill(dist_out, n, nullptr, 1, g_noalloc_sms[dev], st) != cudaSuccess ||
+      launch_init(P, nullptr, 1, st) != cudaSuccess ||
+      launch_delta(P, g_noalloc_sms[dev] * g_noalloc_occ[dev], smem, st) != cudaSuccess) {
+    cudaGetLastError();
+    return OG_E_CUDA;
+  }
+  Sync hs;
+  QState hqs;
+  if (cudaMemcpyAsync(&hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&hqs, qs, sizeof(hqs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return OG_E_CUDA;
+  }
+  if (hs.err & kErrTimeout) return OG_E_TIMEOUT;
+  if (hqs.aborted) return OG_E_ARENA;
+  if (hs.err & kErrSat) return OG_E_OVERFLOW;
+  return OG_OK;
+}
