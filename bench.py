@@ -152,6 +152,32 @@ class ClockSampler:
                 "power_w_max": max(float(r[3] or 0) for r in rows)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of og_delta_kernel from one
+# ncu capture on the road-like 2400 x 2400 graph with 8 sources (the full 4900 x 4900 launch
+# is too large for a multi-pass capture), scaled by vertices x sources to the benchmarked
+# graph.  It describes the kernel sources it was taken on; any other build reports null.
+TRAFFIC_CAPTURE = {"kernel_sha": "f315250d8f211dd3", "bytes": 1.151e9, "n": 5756935,
+                   "sources": 8, "kind": "road"}
+KERNEL_SOURCES = ["paper_1911_07260_gb300/csrc/og_kernels.cu",
+                  "paper_1911_07260_gb300/csrc/og_device.cuh",
+                  "paper_1911_07260_gb300/csrc/og_internal.cuh"]
+
+
+def kernel_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def scaled_traffic(kind: str, n: int, sources: int, engine: int):
+    c = TRAFFIC_CAPTURE
+    if kind != c["kind"] or engine == 2 or kernel_sha() != c["kernel_sha"]:
+        return None
+    return int(c["bytes"] * (n * sources) / (c["n"] * c["sources"]))
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -271,8 +297,10 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / kernel_s / 1e9
+    traffic = scaled_traffic("road" if args.workload == "road-sssp" else "rmat", g.n, nq,
+                             int(eff.engine))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind, "kernel": "og_delta_kernel",
                 "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": round(kernel_s * 1e3, 3)}
@@ -296,6 +324,7 @@ def run_ours(args):
                        "delta": int(eff.delta), "fusion_threshold": int(eff.fusion_threshold),
                        "expand_tile": int(eff.expand_tile),
                        "blocks_per_sm": int(eff.blocks_per_sm),
+                       "engine": "async" if int(eff.engine) == 2 else "rounds",
                        "l2": "inputs larger than L2 (graph %.0f MB + dist %.0f MB > 129 MB)"
                              % ((8 * g.m + 4 * g.n) / 1e6, 4 * nq * g.n / 1e6),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
