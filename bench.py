@@ -61,6 +61,14 @@ def parse_args(argv=None):
                    help="oracle sample size (sources) for the CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--queries", type=int, default=20000, help="serve: queries in the stream")
+    p.add_argument("--rates", type=float, nargs="+", default=[10000.0],
+                   help="serve: Poisson arrival rates (queries/s)")
+    p.add_argument("--slots", type=int, default=128, help="serve: resident query slots")
+    p.add_argument("--budget-us", type=int, default=200, help="serve: time per launch")
+    p.add_argument("--serve-fusion", type=int, default=64, help="serve: fusion threshold")
+    p.add_argument("--sequential", type=int, default=2000,
+                   help="serve: queries in the one-at-a-time baseline")
     return p.parse_args(argv)
 
 
@@ -390,16 +398,222 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- batched and served queries ----------------------------------------------------------
+
+def _oracle_parallel(g, queries, threads: int):
+    """The oracle as it stands on many queries, one host thread per query at a time (the
+    C oracle releases the GIL).  Returns (seconds, results)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(q):
+        kind, s, t = q
+        if kind == "sssp":
+            return oracle.dijkstra(g, s)
+        return oracle.ppsp(g, s, t)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, queries))
+    return time.perf_counter() - t0, res
+
+
+def run_batch(args):
+    """256 concurrent queries on the road-like 1024 x 1024 grid: 128 SSSP + 128 PPSP with
+    targets 10..1000 grid steps away, one persistent launch per step; compared with the
+    same queries run one launch at a time and with the oracle on the host cores."""
+    import torch
+    import graphgen
+    import paper_1911_07260_gb300 as og
+    torch.cuda.init()
+    g = graphgen.road(1024, 0.15, 0.02, seed=1)
+    G = og.Graph.from_csr(g)
+    srcs = graphgen.sample_sources(g, 128, seed=2)
+    pairs = graphgen.sample_pairs_grid_steps(g, 128, 10, 1000, seed=2)
+    cfg = og.autotune(G, og.Q_SSSP, srcs[:8], None, 1 << 8, 1 << 16)
+    queries = [(og.Q_SSSP, int(s), 0, 0) for s in srcs] + \
+              [(og.Q_PPSP, int(a), int(b), 0) for a, b in pairs]
+    nq = len(queries)
+    dbuf = torch.empty(nq * g.n, dtype=torch.int32, device="cuda")
+    _, d_batch, _ = og.batch_run(G, queries, cfg=cfg, out=dbuf)
+    dist_b = dbuf.cpu().numpy().view(np.uint32).reshape(nq, g.n)
+    bytes_step = 0
+    for i, (kind, s, t, _) in enumerate(queries):
+        mr, nr = reached_edges(g, dist_b[i])
+        bytes_step += algo_bytes(mr, nr, g.n)
+    for _ in range(args.warmup):
+        og.batch_run(G, queries, cfg=cfg, out=dbuf)
+    torch.cuda.synchronize()
+    kernel_ns = 0
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, _, st = og.batch_run(G, queries, cfg=cfg, out=dbuf)
+            kernel_ns += st.kernel_ns
+        batch_s = (time.perf_counter() - t0) / args.steps
+    clocks = clk.summary()
+    kernel_s = kernel_ns / 1e9 / args.steps
+    # one launch per query, same schedule, same results
+    one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    exact = True
+    for i, (kind, s, t, _) in enumerate(queries):
+        out, d, _ = og.query_run(G, kind, s, t, 0, cfg=cfg, out=one if kind == og.Q_SSSP else None)
+        if kind == og.Q_SSSP:
+            exact &= bool(np.array_equal(one.cpu().numpy().view(np.uint32), dist_b[i]))
+        else:
+            exact &= int(d) == int(d_batch[i])
+    single_s = time.perf_counter() - t0
+    threads = os.cpu_count() or 1
+    sample = [("sssp", int(s), 0) for s in srcs[:16]] + [("ppsp", int(a), int(b)) for a, b in pairs[:16]]
+    cpu_s, cpu_res = _oracle_parallel(g, sample, threads)
+    for (kind, s, t), r in zip(sample, cpu_res):
+        i = [int(x) for x in srcs[:16]].index(s) if kind == "sssp" else 128 + [
+            (int(a), int(b)) for a, b in pairs[:16]].index((s, t))
+        exact &= bool(np.array_equal(r, dist_b[i])) if kind == "sssp" else int(r) == int(d_batch[i])
+    host = torch.empty(nq * g.n, dtype=torch.int32, pin_memory=True)
+    og.batch_run(G, queries, cfg=cfg, out=host.numpy())
+    t0 = time.perf_counter()
+    for _ in range(max(2, args.steps // 4)):
+        og.batch_run(G, queries, cfg=cfg, out=host.numpy())
+    e2e_s = (time.perf_counter() - t0) / max(2, args.steps // 4)
+    peak, peak_kind = peaks()
+    line = {
+        "metric": "batched queries/s (128 SSSP + 128 PPSP per launch)",
+        "value": round(nq / batch_s, 2), "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(batch_s * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "road-like 1024x1024 grid, 256 queries in one persistent launch",
+                   "n": g.n, "m": g.m, "delta": int(cfg.delta),
+                   "fusion_threshold": int(cfg.fusion_threshold), "engine": int(cfg.engine)},
+        "one_at_a_time": {"value": round(nq / single_s, 2), "unit": "queries/s",
+                          "speedup_batched": round(single_s / batch_s, 2)},
+        "exact_batched_eq_alone_eq_oracle": exact,
+        "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round(bytes_step / kernel_s / 1e9 / peak, 4), "traffic": None,
+                     "peak_source": peak_kind, "kernel_ms": round(kernel_s * 1e3, 3)},
+        "cpu_baseline": {"value": round(len(sample) / cpu_s, 2), "unit": "queries/s",
+                         "cores": threads, "kind": "oracle",
+                         "sample": f"{len(sample)} of the queries (16 SSSP + 16 PPSP), "
+                                   f"{threads} host threads, {cpu_s:.1f} s"},
+        "e2e": {"value": round(nq / e2e_s, 2), "unit": "queries/s", "h2d_bytes_per_step": 16 * nq,
+                "d2h_bytes_per_step": 4 * nq * g.n},
+        "gpu_launches": 3 * args.steps,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Served A*/PPSP on the road-like 4900 x 4900 grid: a seeded Poisson stream of
+    queries (kind by coin, targets log-uniform 10..1000 grid steps away) admitted into a
+    continuous-batching server as slots free up; latency = completion - arrival.  The same
+    arrivals served one query per launch give the baseline."""
+    import torch
+    import graphgen
+    import paper_1911_07260_gb300 as og
+    torch.cuda.init()
+    g = graphgen.road(args.side, 0.15, 0.02, seed=1)
+    G = og.Graph.from_csr(g)
+    total = args.queries
+    pairs = graphgen.sample_pairs_grid_steps(g, total, 10, 1000, seed=2, log_uniform=True)
+    rng = np.random.default_rng(7)
+    kinds = np.where(rng.random(total) < 0.5, og.Q_ASTAR, og.Q_PPSP)
+    tune = og.autotune(G, og.Q_PPSP, pairs[:32, 0], pairs[:32, 1], 1 << 6, 1 << 14)
+    cfg = og.config(delta=int(tune.delta), fusion_threshold=args.serve_fusion)
+    results = {}
+    lines = []
+    for rate in args.rates:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
+        srv = og.Server(G, max_slots=args.slots, cfg=cfg)
+        lat = np.zeros(total)
+        got = np.zeros(total, np.uint32)
+        nxt = done = 0
+        t0 = time.perf_counter()
+        steps = 0
+        while done < total:
+            now = time.perf_counter() - t0
+            while nxt < total and arrivals[nxt] <= now:
+                if not srv.submit(int(kinds[nxt]), int(pairs[nxt, 0]), int(pairs[nxt, 1]), nxt):
+                    break
+                nxt += 1
+            active = srv.step(budget_us=args.budget_us)
+            steps += 1
+            tags, d = srv.poll()
+            if len(tags):
+                tdone = time.perf_counter() - t0
+                lat[tags.astype(np.int64)] = tdone - arrivals[tags.astype(np.int64)]
+                got[tags.astype(np.int64)] = d
+                done += len(tags)
+            if active == 0 and nxt < total and arrivals[nxt] > now:
+                time.sleep(max(0.0, min(arrivals[nxt] - now, 0.001)))
+        wall = time.perf_counter() - t0
+        srv.free()
+        results[rate] = got
+        lines.append({"rate_per_s": rate, "queries_per_s": round(total / wall, 1),
+                      "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                      "steps": steps})
+    # one query per launch, same arrivals (first rate), FIFO order
+    rate = args.rates[0]
+    arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, total))
+    nseq = min(total, args.sequential)
+    lat_s = np.zeros(nseq)
+    seq = np.zeros(nseq, np.uint32)
+    t0 = time.perf_counter()
+    for i in range(nseq):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        s, t = int(pairs[i, 0]), int(pairs[i, 1])
+        seq[i] = og.astar(G, s, t, int(cfg.delta)) if kinds[i] == og.Q_ASTAR else \
+            og.ppsp(G, s, t, int(cfg.delta))
+        lat_s[i] = time.perf_counter() - t0 - arrivals[i]
+    seq_wall = time.perf_counter() - t0
+    exact = all(bool(np.array_equal(results[r][:nseq], seq)) for r in results)
+    import oracle
+    sample = list(range(0, nseq, max(1, nseq // 32)))
+    t0 = time.perf_counter()
+    ref = [oracle.ppsp(g, int(pairs[i, 0]), int(pairs[i, 1])) for i in sample]
+    cpu_s = time.perf_counter() - t0
+    exact &= all(int(seq[i]) == r for i, r in zip(sample, ref))
+    best = max(lines, key=lambda x: x["queries_per_s"])
+    line = {
+        "metric": "served A*/PPSP queries/s with p50/p99 latency",
+        "value": best["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": total,
+        "warmup": 0, "ms_per_step": round(1e3 / max(best["queries_per_s"], 1e-9), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"road-like {args.side}x{args.side} grid, {total} Poisson "
+                               "A*/PPSP queries, continuous batching",
+                   "slots": args.slots, "delta": int(cfg.delta), "budget_us": args.budget_us,
+                   "fusion_threshold": args.serve_fusion},
+        "served": lines,
+        "one_at_a_time": {"rate_per_s": rate, "queries": nseq,
+                          "queries_per_s": round(nseq / seq_wall, 1),
+                          "p50_ms": round(float(np.percentile(lat_s, 50)) * 1e3, 3),
+                          "p99_ms": round(float(np.percentile(lat_s, 99)) * 1e3, 3)},
+        "exact_served_eq_alone_eq_oracle": exact,
+        "cpu_baseline": {"value": round(len(sample) / cpu_s, 2), "unit": "queries/s",
+                         "cores": 1, "kind": "oracle",
+                         "sample": f"{len(sample)} of the queries, Dijkstra stopped at the target"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "road-sssp" or args.workload.startswith("rmat"):
-        run_ours(args)
+    if args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
-        import bench_workloads
-        bench_workloads.main(args)
+        run_ours(args)
 
 
 if __name__ == "__main__":

@@ -305,3 +305,33 @@ def test_ppsp_dirty_ring_reuse(og, orc, gg, road300):
         assert og.ppsp(G, s, t, 256) == orc.ppsp(g, s, t)
         np.testing.assert_array_equal(og.sssp_delta(G, s, 256), orc.dijkstra(g, s))
         np.testing.assert_array_equal(og.sssp_delta(G, t, 16), orc.dijkstra(g, t))
+
+
+def test_server_mix_equals_alone(og, orc, gg, road300):
+    """Continuous batching: queries admitted while others run, stepped with a small time
+    budget so they overlap across launches; every result equals the same query run alone
+    and the oracle."""
+    g, G = road300
+    pairs = gg.sample_pairs_grid_steps(g, 60, 5, 400, seed=33, log_uniform=True)
+    srv = og.Server(G, max_slots=16, cfg=og.config(delta=512, fusion_threshold=64))
+    expect, got = {}, {}
+    pending = list(enumerate(pairs.tolist()))
+    steps = 0
+    while pending or len(got) < len(pairs):
+        while pending:
+            i, (s, t) = pending[0]
+            kind = og.Q_ASTAR if i % 2 else og.Q_PPSP
+            if not srv.submit(kind, s, t, tag=i):
+                break
+            pending.pop(0)
+            expect[i] = (og.astar(G, s, t, 512) if kind == og.Q_ASTAR else og.ppsp(G, s, t, 512))
+        srv.step(budget_us=50)
+        steps += 1
+        tags, d = srv.poll()
+        for tg, dv in zip(tags.tolist(), d.tolist()):
+            got[tg] = dv
+        assert steps < 100000
+    for i, (s, t) in enumerate(pairs.tolist()):
+        assert got[i] == expect[i] == orc.ppsp(g, s, t), i
+    assert srv.free_slots() == srv.max_slots
+    srv.free()
