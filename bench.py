@@ -329,7 +329,9 @@ def run_ours(args):
             "config": {"workload": f"{gname}: {nq} {'SSSP' if kind == og.Q_SSSP else 'wBFS'} "
                                    f"sources per step, one persistent launch",
                        "n": g.n, "m": g.m, "sources_per_gpu": nq,
-                       "delta": int(eff.delta), "fusion_threshold": int(eff.fusion_threshold),
+                       "delta": 1 if kind == og.Q_WBFS else int(eff.delta),
+                       "fusion_threshold": int(eff.fusion_threshold),
+                       "precheck": int(eff.precheck) == 1,
                        "expand_tile": int(eff.expand_tile),
                        "blocks_per_sm": int(eff.blocks_per_sm),
                        "engine": "async" if int(eff.engine) == 2 else "rounds",

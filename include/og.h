@@ -69,6 +69,10 @@ typedef struct og_config {
                                 buckets go to one overflow pile (Section 5.1's lazy
                                 queue idea of a few materialised buckets + overflow)   */
   uint32_t engine;           /* OG_ENGINE_ROUNDS or OG_ENGINE_ASYNC (0 = default: rounds) */
+  uint32_t precheck;         /* read dist[v] before the atomicMin and skip relaxations that
+                                cannot improve: OG_PRECHECK_ON / _OFF (0 = on when the
+                                average degree exceeds 8)                              */
+  uint32_t reserved0;
   uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
   uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
 } og_config;
@@ -82,6 +86,9 @@ typedef struct og_config {
  * by a per-query completion count: each warp fuses its own local bucket, idle warps take
  * over copied buckets, and a query moves to its next bucket the moment its current one
  * has no outstanding entry (rounds counts those bucket transitions). */
+#define OG_PRECHECK_ON 1u
+#define OG_PRECHECK_OFF 2u
+
 #define OG_ENGINE_DEFAULT 0u
 #define OG_ENGINE_ROUNDS 1u
 #define OG_ENGINE_ASYNC 2u

@@ -25,6 +25,7 @@ Q_SSSP, Q_PPSP, Q_ASTAR, Q_WBFS = 0, 1, 2, 3
 FUSION_OFF = 0xFFFFFFFE
 FUSION_UNBOUNDED = 0xFFFFFFFF
 ENGINE_DEFAULT, ENGINE_ROUNDS, ENGINE_ASYNC = 0, 1, 2
+PRECHECK_ON, PRECHECK_OFF = 1, 2
 UNREACHED = 0xFFFFFFFF
 
 
@@ -41,6 +42,7 @@ class Config(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_uint32), ("fusion_threshold", ctypes.c_uint32),
                 ("expand_tile", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("ring_buckets", ctypes.c_uint32), ("engine", ctypes.c_uint32),
+                ("precheck", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("arena_entries", ctypes.c_uint64)]
 
     def as_dict(self):

@@ -220,6 +220,9 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.spin_limit_ns = pick64(u.spin_limit_ns, g->cfg.spin_limit_ns, kDefaultSpinNs);
   r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
   r.engine = u.engine ? u.engine : g->cfg.engine;
+  r.precheck = u.precheck ? u.precheck : g->cfg.precheck;
+  if (!r.precheck)
+    r.precheck = (g->n && (double)g->m / g->n > 8.0) ? OG_PRECHECK_ON : OG_PRECHECK_OFF;
   return r;
 }
 
@@ -321,6 +324,7 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     P.bin_cap = kBinCap;
     P.max_rounds = 0xFFFFFFFFu;
     P.has_astar = astar ? 1u : 0u;
+    P.precheck = c.precheck == OG_PRECHECK_ON ? 1u : 0u;
     P.spin_ns = c.spin_limit_ns;
 
     CK(cudaMemcpyAsync(ws.qd.p, ws.h_qd.p, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, st));
@@ -430,6 +434,7 @@ AParams async_params(const og_graph* g, Workspace& ws, uint32_t* dist, uint32_t 
   P.T = c.fusion_threshold == OG_FUSION_OFF ? 0u : c.fusion_threshold;
   P.lq_cap = kLocalQueue;
   P.has_astar = astar ? 1u : 0u;
+  P.precheck = c.precheck == OG_PRECHECK_ON ? 1u : 0u;
   P.spin_ns = c.spin_limit_ns;
   P.budget_ns = 0;
   return P;
@@ -1070,6 +1075,11 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
   for (uint32_t f : {OG_FUSION_OFF, 256u, 1024u, 2048u, 0xFFFFFFFFu}) {
     og_config c = best;
     c.fusion_threshold = f;
+    consider(c);
+  }
+  for (uint32_t pc : {OG_PRECHECK_ON, OG_PRECHECK_OFF}) {
+    og_config c = best;
+    c.precheck = pc;
     consider(c);
   }
   for (uint32_t t : {32u, 64u, 128u, 256u, 512u}) {

@@ -150,12 +150,22 @@ __device__ __forceinline__ uint32_t relax_async(const AParams& P, WarpQ& L,
     nd[k] = s >= kSat ? kSat : (uint32_t)s;
     if (okk[k] && s >= kSat) atomicOr(&P.sync->err, kErrSat);
   }
+  bool go[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) old[k] = okk[k] ? atomicMin(dq + ew[k].x, nd[k]) : 0u;
+  for (int k = 0; k < K; ++k) go[k] = okk[k];
+  if (P.precheck) {
+    uint32_t seen[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) seen[k] = okk[k] ? ld_cached(dq + ew[k].x) : 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) go[k] = okk[k] && nd[k] < seen[k];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) old[k] = go[k] ? atomicMin(dq + ew[k].x, nd[k]) : 0u;
   uint32_t added = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const bool ins = okk[k] && nd[k] < old[k];
+    const bool ins = go[k] && nd[k] < old[k];
     C.relax += okk[k] ? 1u : 0u;
     C.improved += ins ? 1u : 0u;
     const uint32_t key = ins ? bucket_of(nd[k], h[k], delta) : 0u;

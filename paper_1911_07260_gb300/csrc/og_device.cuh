@@ -71,6 +71,10 @@ __device__ __forceinline__ uint32_t heuristic(const float2* xy, uint32_t integra
   return d >= 4.0e9 ? 4000000000u : (uint32_t)d;
 }
 
+// Cached read of a distance for the pre-check: a stale copy can only be larger than the
+// current value, so "new >= cached" proves the relaxation cannot improve.
+__device__ __forceinline__ uint32_t ld_cached(const uint32_t* p) { return __ldca(p); }
+
 // Priority coarsening (Section 2): bucket = floor(priority / Delta); A* priority is g + h.
 __device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t h, uint32_t delta) {
   if (h == 0) return d / delta;

@@ -108,6 +108,7 @@ struct Params {
   uint32_t bin_cap;       // CTA-local bin capacity per buffer
   uint32_t max_rounds;    // stop (resumably) after this many rounds
   uint32_t has_astar;
+  uint32_t precheck;      // load dist[v] first; atomicMin only if the new value is smaller
   unsigned long long spin_ns;
 };
 
@@ -148,6 +149,7 @@ struct AParams {
   uint32_t T;               // fusion threshold (0 = off)
   uint32_t lq_cap;          // per-warp FIFO capacity (entries)
   uint32_t has_astar;
+  uint32_t precheck;
   unsigned long long spin_ns;
   unsigned long long budget_ns;  // stop (resumably) after this long; 0 = run to the end
 };

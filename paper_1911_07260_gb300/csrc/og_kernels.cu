@@ -136,12 +136,23 @@ __device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins
     nd[k] = s >= kSat ? kSat : (uint32_t)s;
     if (ok[k] && s >= kSat) atomicOr(&P.sync->err, kErrSat);
   }
+  bool go[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) go[k] = ok[k];
+  if (P.precheck) {
+    uint32_t seen[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      seen[k] = ok[k] ? ld_cached(P.dist + (size_t)q[k] * P.n + ew[k].x) : 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) go[k] = ok[k] && nd[k] < seen[k];
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    old[k] = ok[k] ? atomicMin(P.dist + (size_t)q[k] * P.n + ew[k].x, nd[k]) : 0u;
+    old[k] = go[k] ? atomicMin(P.dist + (size_t)q[k] * P.n + ew[k].x, nd[k]) : 0u;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const bool ins = ok[k] && nd[k] < old[k];
+    const bool ins = go[k] && nd[k] < old[k];
     C.relax += ok[k] ? 1u : 0u;
     C.improved += ins ? 1u : 0u;
     const uint32_t key = ins ? bucket_of(nd[k], h[k], S.delta[q[k]]) : 0u;

@@ -335,3 +335,16 @@ def test_server_mix_equals_alone(og, orc, gg, road300):
         assert got[i] == expect[i] == orc.ppsp(g, s, t), i
     assert srv.free_slots() == srv.max_slots
     srv.free()
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("precheck", [1, 2])
+def test_precheck_on_off_identical(og, orc, gg, engine, precheck):
+    """Reading dist[v] before the atomicMin only skips relaxations that cannot improve:
+    distances are unchanged on a skewed and on a road-like graph."""
+    for g in (gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1000, seed=5), gg.road(150, seed=5)):
+        G = og.Graph.from_csr(g)
+        src = int(gg.sample_sources(g, 1, seed=3)[0])
+        got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=og.config(
+            delta=64, precheck=precheck, engine=engine, fusion_threshold=256))
+        np.testing.assert_array_equal(got, orc.dijkstra(g, src))
