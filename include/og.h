@@ -72,7 +72,13 @@ typedef struct og_config {
   uint32_t precheck;         /* read dist[v] before the atomicMin and skip relaxations that
                                 cannot improve: OG_PRECHECK_ON / _OFF (0 = on when the
                                 average degree exceeds 8)                              */
-  uint32_t reserved0;
+  uint32_t layout;           /* adjacency read by the kernels: OG_LAYOUT_CSR, or
+                                OG_LAYOUT_ELL (one 64-byte row of up to 8 edges per
+                                vertex, built at upload when every degree is <= 8;
+                                0 = CSR)                                               */
+  uint32_t prefetch;         /* OG_PREFETCH_ON / _OFF: prefetch an inserted vertex's
+                                adjacency into L2 (0 = off)                           */
+  uint32_t reserved1;
   uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
   uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
 } og_config;
@@ -88,6 +94,10 @@ typedef struct og_config {
  * has no outstanding entry (rounds counts those bucket transitions). */
 #define OG_PRECHECK_ON 1u
 #define OG_PRECHECK_OFF 2u
+#define OG_LAYOUT_CSR 1u
+#define OG_LAYOUT_ELL 2u
+#define OG_PREFETCH_ON 1u
+#define OG_PREFETCH_OFF 2u
 
 #define OG_ENGINE_DEFAULT 0u
 #define OG_ENGINE_ROUNDS 1u
@@ -108,7 +118,9 @@ typedef struct og_stats {
   uint64_t restarts;         /* arena regrowth restarts                                */
   uint64_t kernel_ns;        /* device time of the persistent kernel(s), CUDA events   */
   uint64_t flushes;          /* local buckets copied to a global bucket (fusion limit) */
-  uint64_t reserved[3];
+  uint64_t t_frontier_ns;    /* round engine, summed over CTAs: frontier passes,       */
+  uint64_t t_fused_ns;       /*   fused-round loops,                                   */
+  uint64_t t_barrier_ns;     /*   and grid-barrier waits                               */
 } og_stats;
 
 typedef struct og_query {

@@ -26,6 +26,8 @@ FUSION_OFF = 0xFFFFFFFE
 FUSION_UNBOUNDED = 0xFFFFFFFF
 ENGINE_DEFAULT, ENGINE_ROUNDS, ENGINE_ASYNC = 0, 1, 2
 PRECHECK_ON, PRECHECK_OFF = 1, 2
+LAYOUT_CSR, LAYOUT_ELL = 1, 2
+PREFETCH_ON, PREFETCH_OFF = 1, 2
 UNREACHED = 0xFFFFFFFF
 
 
@@ -42,7 +44,8 @@ class Config(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_uint32), ("fusion_threshold", ctypes.c_uint32),
                 ("expand_tile", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("ring_buckets", ctypes.c_uint32), ("engine", ctypes.c_uint32),
-                ("precheck", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("precheck", ctypes.c_uint32), ("layout", ctypes.c_uint32),
+                ("prefetch", ctypes.c_uint32), ("reserved1", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("arena_entries", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -53,10 +56,11 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("rounds", "fused_iters", "items", "stale", "relax", "improved",
                  "local_inserts", "global_inserts", "overflow_inserts", "redistributions",
-                 "restarts", "kernel_ns", "flushes", "r1", "r2", "r3")]
+                 "restarts", "kernel_ns", "flushes", "t_frontier_ns", "t_fused_ns",
+                 "t_barrier_ns")]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k not in ("r1", "r2", "r3")}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Query(ctypes.Structure):

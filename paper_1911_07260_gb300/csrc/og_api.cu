@@ -20,7 +20,9 @@
 
 namespace og {
 cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st);
-cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem, bool ell);
+cudaError_t launch_ell(const uint32_t* off, const uint2* adj, uint4* ell, uint32_t n, int sms,
+                       cudaStream_t st);
 cudaError_t launch_fill(uint32_t* dist, uint32_t n, const uint32_t* slots, uint32_t nslots,
                         int sms, cudaStream_t st);
 cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots,
@@ -28,7 +30,7 @@ cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots,
 cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj, size_t m,
                               uint32_t n, uint32_t* flags, int sms, cudaStream_t st);
 cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t st);
-cudaError_t async_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t async_occupancy(int* blocks_per_sm, size_t smem, bool ell);
 cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,
                               cudaStream_t st);
 }  // namespace og
@@ -154,6 +156,7 @@ uint32_t pow2_ceil(uint64_t x) {
 }
 
 constexpr uint32_t kDefaultFusion = 1024;
+constexpr int kEllWidthHost = 8;
 constexpr uint32_t kDefaultTile = 128;
 constexpr uint32_t kBinCap = 2048;
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
@@ -167,6 +170,8 @@ struct og_graph {
   double mean_w = 0.0;
   uint32_t* off = nullptr;
   uint2* adj = nullptr;
+  uint4* ell = nullptr;      // ELL-8 rows when every degree is <= 8
+  uint32_t max_deg = 0;
   float2* xy = nullptr;
   std::vector<float> h_xy;   // host copy: target coordinates of A* queries
   bool xy_integral = false;
@@ -175,6 +180,8 @@ struct og_graph {
   int sms = 0;
   int occ = 0;
   int occ_async = 0;
+  int occ_l[2] = {0, 0};        // round engine: CTAs per SM for CSR / ELL
+  int occ_async_l[2] = {0, 0};  // barrier-free engine
 };
 
 struct og_server {
@@ -221,6 +228,11 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
   r.engine = u.engine ? u.engine : g->cfg.engine;
   r.precheck = u.precheck ? u.precheck : g->cfg.precheck;
+  r.layout = u.layout ? u.layout : g->cfg.layout;
+  if (!r.layout) r.layout = OG_LAYOUT_CSR;  // measured faster than ELL on road graphs
+  r.prefetch = u.prefetch ? u.prefetch : (g->cfg.prefetch ? g->cfg.prefetch : OG_PREFETCH_OFF);
+  if (!r.layout || (r.layout == OG_LAYOUT_ELL && !g->ell))
+    r.layout = g->ell ? OG_LAYOUT_ELL : OG_LAYOUT_CSR;
   if (!r.precheck)
     r.precheck = (g->n && (double)g->m / g->n > 8.0) ? OG_PRECHECK_ON : OG_PRECHECK_OFF;
   return r;
@@ -236,18 +248,19 @@ uint32_t ring_size(const og_graph* g, const og_config& c, uint32_t min_delta) {
   return std::max(2u, std::min<uint32_t>(pow2_ceil(span), kMaxRing));
 }
 
-int occupancy(og_graph* g, size_t smem) {
-  if (!g->occ) {
+int occupancy(og_graph* g, size_t smem, bool ell) {
+  if (!g->occ_l[ell]) {
     int dev = 0, b = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
-    CK(delta_occupancy(&b, smem));
+    CK(delta_occupancy(&b, smem, ell));
     if (b < 1) {
       snprintf(g_cuda_msg, sizeof(g_cuda_msg), "persistent kernel does not fit on an SM");
       return OG_E_CUDA;
     }
-    g->occ = b;
+    g->occ_l[ell] = b;
   }
+  g->occ = g->occ_l[ell];
   return OG_OK;
 }
 
@@ -262,7 +275,8 @@ struct RunOut {
 int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
               uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
   const size_t smem = 2 * (size_t)kBinCap * (sizeof(uint2) + sizeof(uint16_t));
-  TRY(occupancy(g, smem));
+  const bool ell = c.layout == OG_LAYOUT_ELL && g->ell;
+  TRY(occupancy(g, smem, ell));
   uint32_t min_delta = 0xFFFFFFFFu;
   bool astar = false;
   for (uint32_t i = 0; i < nq; ++i) {
@@ -302,6 +316,7 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     Params P{};
     P.off = g->off;
     P.adj = g->adj;
+    P.ell = ell ? g->ell : nullptr;
     P.xy = g->xy;
     P.n = g->n;
     P.xy_integral = g->xy_integral ? 1u : 0u;
@@ -325,6 +340,7 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     P.max_rounds = 0xFFFFFFFFu;
     P.has_astar = astar ? 1u : 0u;
     P.precheck = c.precheck == OG_PRECHECK_ON ? 1u : 0u;
+    P.prefetch = c.prefetch == OG_PREFETCH_OFF ? 0u : 1u;
     P.spin_ns = c.spin_limit_ns;
 
     CK(cudaMemcpyAsync(ws.qd.p, ws.h_qd.p, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, st));
@@ -373,18 +389,19 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
 
 constexpr uint32_t kLocalQueue = 512;  // per-warp FIFO entries (barrier-free engine)
 
-int occupancy_async(og_graph* g, size_t smem) {
-  if (!g->occ_async) {
+int occupancy_async(og_graph* g, size_t smem, bool ell) {
+  if (!g->occ_async_l[ell]) {
     int dev = 0, b = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
-    CK(async_occupancy(&b, smem));
+    CK(async_occupancy(&b, smem, ell));
     if (b < 1) {
       snprintf(g_cuda_msg, sizeof(g_cuda_msg), "persistent kernel does not fit on an SM");
       return OG_E_CUDA;
     }
-    g->occ_async = b;
+    g->occ_async_l[ell] = b;
   }
+  g->occ_async = g->occ_async_l[ell];
   return OG_OK;
 }
 
@@ -415,6 +432,7 @@ AParams async_params(const og_graph* g, Workspace& ws, uint32_t* dist, uint32_t 
   AParams P{};
   P.off = g->off;
   P.adj = g->adj;
+  P.ell = (c.layout == OG_LAYOUT_ELL) ? g->ell : nullptr;
   P.xy = g->xy;
   P.n = g->n;
   P.xy_integral = g->xy_integral ? 1u : 0u;
@@ -435,6 +453,7 @@ AParams async_params(const og_graph* g, Workspace& ws, uint32_t* dist, uint32_t 
   P.lq_cap = kLocalQueue;
   P.has_astar = astar ? 1u : 0u;
   P.precheck = c.precheck == OG_PRECHECK_ON ? 1u : 0u;
+  P.prefetch = c.prefetch == OG_PREFETCH_OFF ? 0u : 1u;
   P.spin_ns = c.spin_limit_ns;
   P.budget_ns = 0;
   return P;
@@ -446,7 +465,8 @@ int run_chunk_async(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq,
                     const og_config& c, uint32_t* dist_dev, uint32_t* d_out, Stats* acc,
                     RunOut* ro, cudaStream_t st) {
   const size_t smem = (size_t)kWarps * kLocalQueue * sizeof(uint2);
-  TRY(occupancy_async(g, smem));
+  const bool ell = c.layout == OG_LAYOUT_ELL && g->ell;
+  TRY(occupancy_async(g, smem, ell));
   uint32_t min_delta = 0xFFFFFFFFu;
   bool astar = false;
   for (uint32_t i = 0; i < nq; ++i) {
@@ -567,6 +587,9 @@ void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
   out->restarts = restarts;
   out->kernel_ns = s.v[15];
   out->flushes = s.v[kStFlush];
+  out->t_frontier_ns = s.v[kStTFrontier];
+  out->t_fused_ns = s.v[kStTFused];
+  out->t_barrier_ns = s.v[kStTBarrier];
 }
 
 int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d) {
@@ -726,6 +749,18 @@ int og_graph_upload(const uint64_t* offsets, const uint32_t* neighbors, const ui
     if (hflags[0]) return fail(OG_E_INVALID);  // a neighbor id >= n
     g->min_w = hflags[1];
     g->max_w = hflags[2];
+    for (uint32_t i = 0; i < n; ++i)
+      g->max_deg = std::max<uint32_t>(g->max_deg, (uint32_t)(offsets[i + 1] - offsets[i]));
+    if (g->max_deg <= (uint32_t)kEllWidthHost) {
+      // Low-degree graph: also keep one 64-byte row per vertex (no offsets lookup).
+      if ((e = cudaMalloc(&g->ell, sizeof(uint4) * 4 * (size_t)n)) != cudaSuccess) {
+        g->ell = nullptr;
+        cudaGetLastError();
+      } else if ((e = launch_ell(g->off, g->adj, g->ell, n, g->sms, st)) != cudaSuccess ||
+                 (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        return fail(cuda_fail(e, "build ELL rows"));
+      }
+    }
   } else {
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "upload"));
   }
@@ -793,6 +828,7 @@ void og_graph_free(og_graph* g) {
   g->ws.release();
   if (g->off) cudaFree(g->off);
   if (g->adj) cudaFree(g->adj);
+  if (g->ell) cudaFree(g->ell);
   if (g->xy) cudaFree(g->xy);
   delete g;
 }
@@ -927,7 +963,7 @@ int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active) {
   Workspace& ws = s->ws;
   cudaStream_t st = s->stream;
   const size_t smem = (size_t)kWarps * kLocalQueue * sizeof(uint2);
-  TRY(occupancy_async(g, smem));
+  TRY(occupancy_async(g, smem, s->cfg.layout == OG_LAYOUT_ELL && g->ell));
   bool astar = false;
   uint32_t running = 0;
   for (uint32_t i = 0; i < s->slots; ++i) {
@@ -1080,6 +1116,18 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
   for (uint32_t pc : {OG_PRECHECK_ON, OG_PRECHECK_OFF}) {
     og_config c = best;
     c.precheck = pc;
+    consider(c);
+  }
+  if (g->ell) {
+    for (uint32_t lay : {OG_LAYOUT_CSR, OG_LAYOUT_ELL}) {
+      og_config c = best;
+      c.layout = lay;
+      consider(c);
+    }
+  }
+  for (uint32_t pf : {OG_PREFETCH_ON, OG_PREFETCH_OFF}) {
+    og_config c = best;
+    c.prefetch = pf;
     consider(c);
   }
   for (uint32_t t : {32u, 64u, 128u, 256u, 512u}) {

@@ -121,20 +121,18 @@ __device__ __forceinline__ uint32_t insert_async(const AParams& P, WarpQ& L, boo
 }
 
 template <int K>
-__device__ __forceinline__ uint32_t relax_async(const AParams& P, WarpQ& L,
-                                                const bool (&ok)[K], const uint32_t (&e)[K],
-                                                const uint32_t (&g)[K], ACnt& C,
-                                                uint32_t delta, bool astar, float tx,
-                                                float ty) {
-  uint2 ew[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) ew[k] = ok[k] ? __ldg(P.adj + e[k]) : make_uint2(0u, 0u);
+__device__ __forceinline__ uint32_t relax_edges_async(const AParams& P, WarpQ& L,
+                                                      const bool (&ok)[K],
+                                                      const uint2 (&ew)[K],
+                                                      const uint32_t (&g)[K], ACnt& C,
+                                                      uint32_t delta, bool astar, float tx,
+                                                      float ty) {
   bool okk[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     okk[k] = ok[k];
     if (ok[k] && ew[k].x >= P.n) {
-      report_bad(P.sync, 3u, ew[k].x, e[k]);
+      report_bad(P.sync, 3u, ew[k].x, 0u);
       okk[k] = false;
     }
   }
@@ -168,15 +166,29 @@ __device__ __forceinline__ uint32_t relax_async(const AParams& P, WarpQ& L,
     const bool ins = go[k] && nd[k] < old[k];
     C.relax += okk[k] ? 1u : 0u;
     C.improved += ins ? 1u : 0u;
+    if (ins && P.prefetch) prefetch_row(P.ell, P.off, ew[k].x);
     const uint32_t key = ins ? bucket_of(nd[k], h[k], delta) : 0u;
     added += insert_async(P, L, ins, ew[k].x, nd[k], key, C);
   }
   return added;
 }
 
+template <int K>
+__device__ __forceinline__ uint32_t relax_async(const AParams& P, WarpQ& L,
+                                                const bool (&ok)[K], const uint32_t (&e)[K],
+                                                const uint32_t (&g)[K], ACnt& C,
+                                                uint32_t delta, bool astar, float tx,
+                                                float ty) {
+  uint2 ew[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) ew[k] = ok[k] ? __ldg(P.adj + e[k]) : make_uint2(0u, 0u);
+  return relax_edges_async<K>(P, L, ok, ew, g, C, delta, astar, tx, ty);
+}
+
 // Relaxes the out-edges of the entries held by the lanes (query L.q, bucket L.cur).  An
 // entry whose vertex has a smaller distance by now is skipped (a newer entry exists).
 // Returns the number of current-bucket entries added.
+template <bool ELL>
 __device__ uint32_t expand_async(const AParams& P, WarpQ& L, bool has, uint32_t u, uint32_t g,
                                  ACnt& C) {
   const uint32_t lane = threadIdx.x & 31;
@@ -188,6 +200,31 @@ __device__ uint32_t expand_async(const AParams& P, WarpQ& L, bool has, uint32_t 
   if (has && (u >= P.n || L.q >= P.nq)) {
     report_bad(P.sync, 1u, u, L.q);
     has = false;
+  }
+  if (ELL) {  // ELL rows: one 64-byte row per lane, no offsets lookup
+    uint2 ew[kEllWidth];
+    bool live = has;
+    uint32_t d = 0;
+    if (has) {
+      C.items++;
+      d = __ldcg(P.dist + (size_t)L.q * P.n + u);
+      load_row(P.ell, u, ew);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kEllWidth; ++k) ew[k] = make_uint2(kNone, 0u);
+    }
+    if (has && d < g) {
+      live = false;
+      C.stale++;
+    }
+    bool ok[kEllWidth];
+    uint32_t gg[kEllWidth];
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k) {
+      ok[k] = live && ew[k].x != kNone;
+      gg[k] = g;
+    }
+    return relax_edges_async<kEllWidth>(P, L, ok, ew, gg, C, delta, astar, tx, ty);
   }
   if (has) {
     C.items++;
@@ -551,7 +588,8 @@ __device__ bool claim(const AParams& P, uint32_t& rot, uint32_t& q, uint32_t& mo
   return true;
 }
 
-extern "C" __global__ void __launch_bounds__(kBlock) og_async_kernel(AParams P) {
+template <bool ELL>
+__device__ __forceinline__ void async_body(const AParams& P) {
   extern __shared__ __align__(16) unsigned char og_async_smem[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpQ L;
@@ -582,7 +620,7 @@ extern "C" __global__ void __launch_bounds__(kBlock) og_async_kernel(AParams P) 
       __syncwarp();
       L.head = (L.head + k) % L.cap;
       L.size -= k;
-      const uint32_t added = expand_async(P, L, has, v, d, C);
+      const uint32_t added = expand_async<ELL>(P, L, has, v, d, C);
       C.fused++;
       settle(P, L.q, added - k);
       if (L.size && L.size >= P.T) flush_local(P, L, C, 32u);
@@ -633,7 +671,7 @@ extern "C" __global__ void __launch_bounds__(kBlock) og_async_kernel(AParams P) 
         }
         L.q = q;
         L.cur = cur;
-        const uint32_t added = expand_async(P, L, has, v, d, C);
+        const uint32_t added = expand_async<ELL>(P, L, has, v, d, C);
         settle(P, q, added - k);
         if (L.size && L.size >= P.T) flush_local(P, L, C, 32u);
       } else {
@@ -680,6 +718,13 @@ extern "C" __global__ void __launch_bounds__(kBlock) og_async_kernel(AParams P) 
   }
 }
 
+extern "C" __global__ void __launch_bounds__(kBlock) og_async_kernel(AParams P) {
+  async_body<false>(P);
+}
+extern "C" __global__ void __launch_bounds__(kBlock) og_async_ell_kernel(AParams P) {
+  async_body<true>(P);
+}
+
 // Starts the listed queries: dist[src] = 0 and the start vertex as the only entry of its
 // first bucket (the initial state of the Section 3.2 figures).
 extern "C" __global__ void og_async_init_kernel(AParams P, const uint32_t* slots,
@@ -721,16 +766,16 @@ extern "C" __global__ void og_async_init_kernel(AParams P, const uint32_t* slots
 }
 
 cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t st) {
-  og_async_kernel<<<grid, kBlock, smem, st>>>(P);
+  if (P.ell) og_async_ell_kernel<<<grid, kBlock, smem, st>>>(P);
+  else og_async_kernel<<<grid, kBlock, smem, st>>>(P);
   return cudaGetLastError();
 }
 
-cudaError_t async_occupancy(int* blocks_per_sm, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute((const void*)og_async_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t async_occupancy(int* blocks_per_sm, size_t smem, bool ell) {
+  const void* k = ell ? (const void*)og_async_ell_kernel : (const void*)og_async_kernel;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                       (const void*)og_async_kernel, kBlock, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
 }
 
 cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,

@@ -71,6 +71,32 @@ __device__ __forceinline__ uint32_t heuristic(const float2* xy, uint32_t integra
   return d >= 4.0e9 ? 4000000000u : (uint32_t)d;
 }
 
+constexpr int kEllWidth = 8;  // edges per ELL row (64 bytes)
+
+// Brings a vertex's adjacency into L2 ahead of its expansion.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_row(const uint4* ell, const uint32_t* off, uint32_t v) {
+  if (ell) {
+    const uint4* r = ell + (size_t)v * 4;
+    prefetch_l2(r);
+    prefetch_l2(r + 2);
+  } else {
+    prefetch_l2(off + v);
+  }
+}
+
+// Loads one ELL row: up to 8 {neighbor, weight} pairs in four 16-byte loads.
+__device__ __forceinline__ void load_row(const uint4* ell, uint32_t v, uint2 (&ew)[kEllWidth]) {
+  const uint4* r = ell + (size_t)v * 4;
+  const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+  ew[0] = make_uint2(a.x, a.y); ew[1] = make_uint2(a.z, a.w);
+  ew[2] = make_uint2(b.x, b.y); ew[3] = make_uint2(b.z, b.w);
+  ew[4] = make_uint2(c.x, c.y); ew[5] = make_uint2(c.z, c.w);
+  ew[6] = make_uint2(d.x, d.y); ew[7] = make_uint2(d.z, d.w);
+}
+
 // Cached read of a distance for the pre-check: a stale copy can only be larger than the
 // current value, so "new >= cached" proves the relaxation cannot improve.
 __device__ __forceinline__ uint32_t ld_cached(const uint32_t* p) { return __ldca(p); }

@@ -80,13 +80,17 @@ struct Sync {
 
 enum StatIdx {
   kStRounds, kStFused, kStItems, kStStale, kStRelax, kStImproved, kStLocal, kStGlobal,
-  kStOvf, kStRedist, kStFlush, kStCount
+  kStOvf, kStRedist, kStFlush,
+  kStTFrontier, kStTFused, kStTBarrier,  // ns summed over CTAs (round engine)
+  kStCount
 };
 struct Stats { unsigned long long v[16]; };
 
 struct Params {
   const uint32_t* off;
   const uint2* adj;
+  const uint4* ell;       // ELL-8 rows (64 B per vertex, unused slots have neighbor
+                          // 0xFFFFFFFF) or null: then offsets + adj are used
   const float2* xy;
   uint32_t n;
   uint32_t xy_integral;   // coordinates integral and < 2^24 in magnitude
@@ -109,6 +113,7 @@ struct Params {
   uint32_t max_rounds;    // stop (resumably) after this many rounds
   uint32_t has_astar;
   uint32_t precheck;      // load dist[v] first; atomicMin only if the new value is smaller
+  uint32_t prefetch;      // prefetch an inserted vertex's adjacency into L2
   unsigned long long spin_ns;
 };
 
@@ -132,6 +137,7 @@ struct AQState {
 struct AParams {
   const uint32_t* off;
   const uint2* adj;
+  const uint4* ell;
   const float2* xy;
   uint32_t n;
   uint32_t xy_integral;
@@ -150,6 +156,7 @@ struct AParams {
   uint32_t lq_cap;          // per-warp FIFO capacity (entries)
   uint32_t has_astar;
   uint32_t precheck;
+  uint32_t prefetch;
   unsigned long long spin_ns;
   unsigned long long budget_ns;  // stop (resumably) after this long; 0 = run to the end
 };

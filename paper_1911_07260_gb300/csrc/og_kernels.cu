@@ -32,6 +32,7 @@ struct Smem {
   uint32_t err;
   uint32_t f_active, f_redist;
   uint32_t wtmp[kWarps + 1];
+  unsigned long long t_front, t_fused, t_bar;  // per-CTA phase time (thread 0)
 };
 
 struct Bins {
@@ -112,21 +113,23 @@ __device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins
 // improvement is inserted eagerly into bucket floor((nd + h) / Delta).  All K neighbor
 // loads are issued before any atomic and all K atomics before any insert, so a lane keeps
 // K independent memory operations in flight instead of paying one round trip per edge.
+// Relaxes up to K already-loaded edges per lane: nd = g + w (saturating), atomicMin on
+// dist[v]; an improvement is inserted eagerly into bucket floor((nd + h) / Delta).  All K
+// atomics are issued before any insert, so a lane keeps K independent memory operations
+// in flight instead of paying one round trip per edge.
 template <int K>
-__device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins& B, int out,
+__device__ __forceinline__ void relax_edges(const Params& P, Smem& S, const Bins& B, int out,
                                             bool allow_local, const bool (&ok)[K],
-                                            const uint32_t (&e)[K], const uint32_t (&g)[K],
+                                            const uint2 (&ew)[K], const uint32_t (&g)[K],
                                             const uint32_t (&q)[K], Cnt& C) {
-  uint2 ew[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) ew[k] = ok[k] ? __ldg(P.adj + e[k]) : make_uint2(0u, 0u);
   uint32_t h[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     h[k] = 0;
     if (P.has_astar && ok[k]) {
       const QDesc* d = P.qd + q[k];
-      if (__ldg(&d->kind) == kASTAR) h[k] = heuristic(P.xy, P.xy_integral, ew[k].x, __ldg(&d->tx), __ldg(&d->ty));
+      if (__ldg(&d->kind) == kASTAR)
+        h[k] = heuristic(P.xy, P.xy_integral, ew[k].x, __ldg(&d->tx), __ldg(&d->ty));
     }
   }
   uint32_t nd[K], old[K];
@@ -155,9 +158,22 @@ __device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins
     const bool ins = go[k] && nd[k] < old[k];
     C.relax += ok[k] ? 1u : 0u;
     C.improved += ins ? 1u : 0u;
+    if (ins && P.prefetch) prefetch_row(P.ell, P.off, ew[k].x);
     const uint32_t key = ins ? bucket_of(nd[k], h[k], S.delta[q[k]]) : 0u;
     insert_warp(P, S, B, out, ins, allow_local, ew[k].x, nd[k], key, q[k], C);
   }
+}
+
+// CSR edges: the K neighbor loads are issued together, then relax_edges.
+template <int K>
+__device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins& B, int out,
+                                            bool allow_local, const bool (&ok)[K],
+                                            const uint32_t (&e)[K], const uint32_t (&g)[K],
+                                            const uint32_t (&q)[K], Cnt& C) {
+  uint2 ew[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) ew[k] = ok[k] ? __ldg(P.adj + e[k]) : make_uint2(0u, 0u);
+  relax_edges<K>(P, S, B, out, allow_local, ok, ew, g, q, C);
 }
 
 constexpr int kLightBatch = 4;  // light-edge groups of 32 relaxed per batch
@@ -168,10 +184,40 @@ constexpr int kHeavyBatch = 4;  // groups of 32 edges of one heavy vertex per ba
 // Vertices with >= 32 edges are expanded by the whole warp one at a time; the others are
 // flattened into one edge list that the 32 lanes walk together, so consecutive lanes
 // read consecutive edges of a vertex.  Must be called by all 32 lanes.
+template <bool ELL>
 __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins& B, int out,
                                             bool allow_local, bool has, uint32_t u,
                                             uint32_t g, uint32_t q, Cnt& C) {
   const uint32_t lane = threadIdx.x & 31;
+  if (ELL) {
+    // ELL rows: each lane reads its vertex's whole row (64 bytes, no offsets lookup) in
+    // parallel with the stale check and relaxes its up to 8 edges together.
+    uint2 ew[kEllWidth];
+    bool live = has;
+    uint32_t d = 0;
+    if (has) {
+      C.items++;
+      d = __ldcg(P.dist + (size_t)q * P.n + u);
+      load_row(P.ell, u, ew);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kEllWidth; ++k) ew[k] = make_uint2(kNone, 0u);
+    }
+    if (has && d != g) {
+      live = false;
+      C.stale++;
+    }
+    bool ok[kEllWidth];
+    uint32_t gg[kEllWidth], qq[kEllWidth];
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k) {
+      ok[k] = live && ew[k].x != kNone;
+      gg[k] = g;
+      qq[k] = q;
+    }
+    relax_edges<kEllWidth>(P, S, B, out, allow_local, ok, ew, gg, qq, C);
+    return;
+  }
   uint32_t beg = 0, end = 0;
   if (has) {
     C.items++;
@@ -407,6 +453,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
 // (setting kErrTimeout) after spin_ns nanoseconds or as soon as a fatal error is posted.
 __device__ void grid_barrier(const Params& P, Smem& S, uint32_t& bar, uint32_t done_phase) {
   __syncthreads();
+  const uint64_t t_in = threadIdx.x == 0 ? gtimer() : 0ull;
   if (threadIdx.x == 0) {
     __threadfence();
     const uint32_t a = atomicAdd(&P.sync->arrive, 1u);
@@ -438,13 +485,16 @@ __device__ void grid_barrier(const Params& P, Smem& S, uint32_t& bar, uint32_t d
   if (threadIdx.x == 0) {
     S.phase = ld_acquire(&P.sync->phase);
     S.err = ld_relaxed(&P.sync->err);
+    S.t_bar += gtimer() - t_in;
   }
   __syncthreads();
   ++bar;
 }
 
 // One round for all active queries: frontier pass over the global current buckets, then
-// the CTA-local fusion loop (Section 3.3).
+// the CTA-local fusion loop (Section 3.3): the CTA's warps drain its local bin together,
+// one level per iteration, with block-level synchronisation only.
+template <bool ELL>
 __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uint32_t& fused) {
   const uint32_t tid = threadIdx.x;
   for (uint32_t q = tid; q < P.nq; q += kBlock) {
@@ -460,6 +510,7 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
   __syncthreads();
   const uint32_t total = S.pref[P.nq];
   const bool fuse = P.T != 0;
+  const uint64_t t_start = tid == 0 ? gtimer() : 0ull;
   for (;;) {
     if (tid == 0) S.grab = atomicAdd(&P.sync->work, P.tile);
     __syncthreads();
@@ -483,9 +534,11 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
         u = en.x;
         g = en.y;
       }
-      expand_warp(P, S, B, 0, fuse, has, u, g, q, C);
+      expand_warp<ELL>(P, S, B, 0, fuse, has, u, g, q, C);
     }
   }
+  const uint64_t t_mid = tid == 0 ? gtimer() : 0ull;
+  if (tid == 0) S.t_front += t_mid - t_start;
   if (!fuse) return;
   int in = 0;
   for (;;) {
@@ -518,7 +571,7 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
         en = B.e[in][k];
         q = B.q[in][k];
       }
-      expand_warp(P, S, B, in ^ 1, true, has, en.x, en.y, q, C);
+      expand_warp<ELL>(P, S, B, in ^ 1, true, has, en.x, en.y, q, C);
     }
     __syncthreads();
     if (tid == 0) S.binN[in] = 0;
@@ -526,6 +579,7 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
     ++fused;
   }
   __syncthreads();
+  if (tid == 0) S.t_fused += gtimer() - t_mid;
 }
 
 // Overflow redistribution, step 1: the smallest bucket among live pile entries.
@@ -596,7 +650,8 @@ __device__ void redist_move_phase(const Params& P) {
   }
 }
 
-extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
+template <bool ELL>
+__device__ __forceinline__ void delta_body(const Params& P) {
   extern __shared__ __align__(16) unsigned char og_dyn_smem[];
   __shared__ Smem S;
   Bins B;
@@ -608,11 +663,12 @@ extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
   Cnt C = {0, 0, 0, 0, 0, 0, 0};
   uint32_t fused = 0;
   uint32_t bar = 0;
+  if (threadIdx.x == 0) S.t_front = S.t_fused = S.t_bar = 0ull;
   grid_barrier(P, S, bar, kPhPrologue);
   for (;;) {
     const uint32_t phase = S.phase;
     if (phase == kPhStop || (S.err & kErrFatal)) break;
-    if (phase == kPhRelax) relax_phase(P, S, B, C, fused);
+    if (phase == kPhRelax) relax_phase<ELL>(P, S, B, C, fused);
     else if (phase == kPhRedistMin) redist_min_phase(P);
     else if (phase == kPhRedistMove) redist_move_phase(P);
     grid_barrier(P, S, bar, phase);
@@ -625,7 +681,21 @@ extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
     const uint32_t s = warp_sum(vals[k]);
     if (lane == 0 && s) atomicAdd(&P.stats->v[idx[k]], (unsigned long long)s);
   }
-  if (threadIdx.x == 0 && fused) atomicAdd(&P.stats->v[kStFused], (unsigned long long)fused);
+  if (threadIdx.x == 0) {
+    if (fused) atomicAdd(&P.stats->v[kStFused], (unsigned long long)fused);
+    atomicAdd(&P.stats->v[kStTFrontier], S.t_front);
+    atomicAdd(&P.stats->v[kStTFused], S.t_fused);
+    atomicAdd(&P.stats->v[kStTBarrier], S.t_bar);
+  }
+}
+
+// The persistent kernel, one instantiation per adjacency layout (CSR offsets + edge
+// array for any graph; ELL-8 rows for graphs of degree at most 8).
+extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
+  delta_body<false>(P);
+}
+extern "C" __global__ void __launch_bounds__(kBlock) og_delta_ell_kernel(Params P) {
+  delta_body<true>(P);
 }
 
 // dist[slot][*] = unreachable for the listed slots (blockIdx.y indexes the slot list).
@@ -707,19 +777,42 @@ extern "C" __global__ void og_interleave_kernel(const uint32_t* nbr, const uint3
 
 namespace og {
 
+// ELL-8 rows from CSR: row v holds v's out-edges in its first deg(v) slots and the
+// neighbor marker 0xFFFFFFFF in the rest (only built for graphs of degree <= 8).
+extern "C" __global__ void og_ell_kernel(const uint32_t* off, const uint2* adj, uint4* ell,
+                                         uint32_t n) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const uint32_t beg = off[v], end = off[v + 1];
+    uint2 e[kEllWidth];
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k)
+      e[k] = beg + k < end ? adj[beg + k] : make_uint2(kNone, 0u);
+    uint4* r = ell + (size_t)v * 4;
+    r[0] = make_uint4(e[0].x, e[0].y, e[1].x, e[1].y);
+    r[1] = make_uint4(e[2].x, e[2].y, e[3].x, e[3].y);
+    r[2] = make_uint4(e[4].x, e[4].y, e[5].x, e[5].y);
+    r[3] = make_uint4(e[6].x, e[6].y, e[7].x, e[7].y);
+  }
+}
+
+cudaError_t launch_ell(const uint32_t* off, const uint2* adj, uint4* ell, uint32_t n, int sms,
+                       cudaStream_t st) {
+  og_ell_kernel<<<sms * 8, 256, 0, st>>>(off, adj, ell, n);
+  return cudaGetLastError();
+}
+
 // Host-side launchers (the kernels above are only launched through these).
 cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P)};
-  return cudaLaunchCooperativeKernel((const void*)og_delta_kernel, dim3(grid), dim3(kBlock),
-                                     args, smem, st);
+  const void* k = P.ell ? (const void*)og_delta_ell_kernel : (const void*)og_delta_kernel;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kBlock), args, smem, st);
 }
 
-cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute((const void*)og_delta_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem, bool ell) {
+  const void* k = ell ? (const void*)og_delta_ell_kernel : (const void*)og_delta_kernel;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)og_delta_kernel,
-                                                       kBlock, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
 }
 
 cudaError_t launch_fill(uint32_t* dist, uint32_t n, const uint32_t* slots, uint32_t nslots,
@@ -804,7 +897,7 @@ extern "C" int og_sssp_delta_noalloc(const uint32_t* offsets, const uint32_t* ed
         return OG_E_CUDA;
       }
       int occ = 0, sms = 0;
-      if (delta_occupancy(&occ, smem) != cudaSuccess || occ < 1 ||
+      if (delta_occupancy(&occ, smem, false) != cudaSuccess || occ < 1 ||
           cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return OG_E_CUDA;

@@ -348,3 +348,22 @@ def test_precheck_on_off_identical(og, orc, gg, engine, precheck):
         got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=og.config(
             delta=64, precheck=precheck, engine=engine, fusion_threshold=256))
         np.testing.assert_array_equal(got, orc.dijkstra(g, src))
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_csr_and_ell_layouts_identical(og, orc, gg, engine):
+    """Graphs of degree <= 8 also get ELL rows (no offsets lookup); both layouts give the
+    oracle's distances, for SSSP and for PPSP / A*."""
+    g = gg.road(200, seed=11)
+    G = og.Graph.from_csr(g)
+    src = int(gg.sample_sources(g, 1, seed=4)[0])
+    ref = orc.dijkstra(g, src)
+    pairs = gg.sample_pairs_grid_steps(g, 6, 5, 150, seed=8)
+    for layout in (og.LAYOUT_CSR, og.LAYOUT_ELL):
+        cfg = og.config(delta=1024, layout=layout, engine=engine, fusion_threshold=128)
+        got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=cfg)
+        np.testing.assert_array_equal(got, ref)
+        for s, t in pairs.tolist():
+            for kind in (og.Q_PPSP, og.Q_ASTAR):
+                _, d, _ = og.query_run(G, kind, s, t, cfg=cfg)
+                assert d == orc.ppsp(g, s, t)
