@@ -65,7 +65,7 @@ typedef struct og_config {
                                 OG_FUSION_OFF disables fusion, 0xFFFFFFFF = unbounded   */
   uint32_t expand_tile;      /* frontier entries a CTA claims per grab (multiple of 32) */
   uint32_t blocks_per_sm;    /* persistent CTAs per SM (capped by occupancy)           */
-  uint32_t ring_buckets;     /* materialised buckets (power of two, <= 64); further
+  uint32_t ring_buckets;     /* materialised buckets (power of two, <= 256); further
                                 buckets go to one overflow pile (Section 5.1's lazy
                                 queue idea of a few materialised buckets + overflow)   */
   uint32_t engine;           /* OG_ENGINE_ROUNDS or OG_ENGINE_ASYNC (0 = default: rounds) */

@@ -106,7 +106,7 @@ struct HBuf {
 
 // Device scratch of one launch configuration (grown on demand, reused across calls).
 struct Workspace {
-  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq;
+  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big;
   HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // Barrier-free engine: ring positions must read "free" (all ones) before use.  Entries
@@ -115,7 +115,8 @@ struct Workspace {
   std::vector<std::pair<uint64_t, uint64_t>> dirty;
   void* ring_ptr = nullptr;
   void release() {
-    for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq})
+    for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
+                    &big})
       b->release();
     for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq}) b->release();
     clean_upto = 0;
@@ -238,6 +239,23 @@ og_config resolve(const og_graph* g, const og_config* user) {
   return r;
 }
 
+// Default bucket arena per query: large enough that buckets rarely spill into the
+// overflow pile (a spill costs two grid-wide redistribution passes) -- 48n entries for
+// dense graphs, 12n otherwise -- within 60% of the free device memory shared by the nq
+// queries of a launch, and at least 6n entries.
+uint64_t default_arena(const og_graph* g, uint32_t nq) {
+  const uint64_t lo = std::max<uint64_t>(6ull * g->n, 1ull << 16);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return lo;
+  }
+  const uint64_t budget = (uint64_t)((double)fr * 0.6) / sizeof(uint2) / std::max(1u, nq);
+  // Dense graphs have large buckets spread over many materialised slots.
+  const uint64_t want = (g->n && (double)g->m / g->n > 8.0 ? 48ull : 12ull) * g->n;
+  return std::max(lo, std::min<uint64_t>(want, budget));
+}
+
 uint32_t ring_size(const og_graph* g, const og_config& c, uint32_t min_delta) {
   if (c.ring_buckets) {
     uint32_t b = pow2_ceil(c.ring_buckets);
@@ -284,8 +302,7 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     astar |= qd[i].kind == kASTAR;
   }
   const uint32_t B = ring_size(g, c, min_delta);
-  uint64_t entries = c.arena_entries ? c.arena_entries
-                                     : std::max<uint64_t>(6ull * g->n, 1ull << 16);
+  uint64_t entries = c.arena_entries ? c.arena_entries : default_arena(g, nq);
   TRY(ws.events());
   TRY(ws.h_qd.ensure(sizeof(QDesc) * nq));
   TRY(ws.h_qs.ensure(sizeof(QState) * nq));
@@ -312,6 +329,8 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     TRY(ws.slots.ensure(sizeof(uint32_t) * nq));
     TRY(ws.h_slots.ensure(sizeof(uint32_t) * nq));
     memcpy(ws.h_slots.p, pending.data(), sizeof(uint32_t) * np);
+    const uint32_t big_cap = g->max_deg >= kBigDegree ? 65536u : 0u;
+    if (big_cap) TRY(ws.big.ensure(sizeof(BigItem) * big_cap));
 
     Params P{};
     P.off = g->off;
@@ -329,6 +348,8 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     P.fr_pref = ws.pref.as<uint32_t>();
     P.sync = ws.sync.as<Sync>();
     P.stats = ws.stats.as<Stats>();
+    P.big = big_cap ? ws.big.as<BigItem>() : nullptr;
+    P.big_cap = big_cap;
     P.nq = nq;
     P.B = B;
     P.Bmask = B - 1;
@@ -474,8 +495,7 @@ int run_chunk_async(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq,
     astar |= qd[i].kind == kASTAR;
   }
   const uint32_t B = ring_size(g, c, min_delta);
-  uint64_t entries = c.arena_entries ? c.arena_entries
-                                     : std::max<uint64_t>(6ull * g->n, 1ull << 16);
+  uint64_t entries = c.arena_entries ? c.arena_entries : default_arena(g, nq);
   TRY(ws.events());
   TRY(ws.h_qd.ensure(sizeof(QDesc) * nq));
   TRY(ws.h_aq.ensure(sizeof(AQState) * nq));

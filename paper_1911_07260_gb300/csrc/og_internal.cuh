@@ -22,7 +22,7 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;  // no target
 constexpr int kBlock = 256;              // threads per persistent CTA
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxQ = 512;               // queries per launch
-constexpr int kMaxRing = 64;             // materialised buckets per query
+constexpr int kMaxRing = 256;            // materialised buckets per query
 
 enum Kind : uint32_t { kSSSP = 0, kPPSP = 1, kASTAR = 2 };
 
@@ -32,6 +32,16 @@ enum Phase : uint32_t {
   kPhRedistMove = 2, // overflow pile: move entries of the new ring window into the ring
   kPhStop = 3,
   kPhPrologue = 4,   // kernel start: publish the frontier of the current state
+  kPhBig = 5,        // edges of very-high-degree vertices, split over all CTAs
+};
+
+// A vertex whose out-degree is at least kBigDegree (a hub of a skewed graph) is not
+// expanded by one warp: it is listed, and after the round every CTA claims 1024-edge
+// chunks of it.
+constexpr uint32_t kBigDegree = 32768;
+constexpr uint32_t kBigChunk = 1024;
+struct BigItem {
+  uint32_t u, g, q, beg, end, next;
 };
 
 enum ErrBits : uint32_t { kErrTimeout = 1, kErrArena = 2, kErrSat = 4, kErrBounds = 8 };
@@ -70,12 +80,13 @@ struct Sync {
   uint32_t rounds;       // rounds run in this launch
   uint32_t any_active;
   uint32_t active;       // barrier-free engine: queries not yet finished
+  uint32_t big_n;        // listed very-high-degree vertices (round engine)
   uint32_t bad_code;     // first failed internal bounds check (0 = none)
   uint32_t bad_val;      // the offending value
   uint32_t bad_aux;      // context (query or position)
   uint32_t progress;     // barrier-free engine: heartbeat of busy warps
   uint32_t timeout_at;   // which bounded wait gave up (1 idle, 2 entry hand-off)
-  uint32_t pad[2];
+  uint32_t pad[1];
 };
 
 enum StatIdx {
@@ -103,6 +114,8 @@ struct Params {
   uint32_t* fr_pref;      // nq + 1 prefix sums of the frontier sizes
   Sync* sync;
   Stats* stats;
+  BigItem* big;           // very-high-degree vertices of the current round (or null)
+  uint32_t big_cap;
   uint32_t nq;
   uint32_t B, Bmask;
   uint32_t cap;           // entries per ring slot

@@ -231,7 +231,22 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
     }
   }
   const uint32_t deg = end - beg;
-  const bool heavy = deg >= 32u;
+  if (deg >= kBigDegree && P.big) {
+    // Hub: list it; all CTAs split its edges after the round.
+    const uint32_t slot = atomicAdd(&P.sync->big_n, 1u);
+    if (slot < P.big_cap) {
+      BigItem it;
+      it.u = u;
+      it.g = g;
+      it.q = q;
+      it.beg = beg;
+      it.end = end;
+      it.next = 0;
+      P.big[slot] = it;
+      beg = end = 0;
+    }
+  }
+  const bool heavy = end - beg >= 32u;
   unsigned hm = __ballot_sync(FULL, heavy);
   while (hm) {
     const int l = __ffs(hm) - 1;
@@ -251,7 +266,7 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
       relax_batch<kHeavyBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
     }
   }
-  const uint32_t ld = heavy ? 0u : deg;
+  const uint32_t ld = heavy ? 0u : end - beg;
   uint32_t incl = ld;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -323,6 +338,18 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
   Sync* sy = P.sync;
   const uint32_t err = ld_relaxed(&sy->err);
   const bool fatal = (err & kErrFatal) != 0;
+  if (done_phase == kPhRelax && !fatal && __ldcg(&sy->big_n) > 0u) {
+    // Listed hubs first: the same round continues with the BIG phase.
+    if (tid == 0) {
+      sy->phase = kPhBig;
+      sy->work = 0;
+    }
+    return;
+  }
+  if (done_phase == kPhBig) {
+    if (tid == 0) sy->big_n = 0;
+    done_phase = kPhRelax;
+  }
   if (tid == 0) {
     S.f_active = 0;
     S.f_redist = 0;
@@ -650,6 +677,42 @@ __device__ void redist_move_phase(const Params& P) {
   }
 }
 
+// The BIG phase: every CTA walks the list of hubs of this round and claims 1024-edge
+// chunks of each (8 warps x 4 groups of 32 edges), so one hub no longer holds up a round.
+// Improved vertices go to the global buckets.
+__device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
+  __syncthreads();
+  const uint32_t n = min(__ldcg(&P.sync->big_n), P.big_cap);
+  for (uint32_t i = 0; i < n; ++i) {
+    BigItem* it = P.big + i;
+    const uint32_t hb = __ldcg(&it->beg), he = __ldcg(&it->end);
+    const uint32_t hg = __ldcg(&it->g), hq = __ldcg(&it->q);
+    for (;;) {
+      if (tid == 0) {
+        // one read skips a hub whose edges are all claimed already
+        S.grab = __ldcg(&it->next) >= he - hb ? he - hb : atomicAdd(&it->next, kBigChunk);
+      }
+      __syncthreads();
+      const uint32_t c = S.grab;
+      __syncthreads();
+      if (c >= he - hb) break;
+      const uint32_t e0 = hb + c + warp * (kBigChunk / kWarps);
+      bool ok[kHeavyBatch];
+      uint32_t ee[kHeavyBatch], gg[kHeavyBatch], qq[kHeavyBatch];
+#pragma unroll
+      for (int k = 0; k < kHeavyBatch; ++k) {
+        ee[k] = e0 + 32u * k + lane;
+        ok[k] = ee[k] < he && ee[k] < hb + c + kBigChunk;
+        gg[k] = hg;
+        qq[k] = hq;
+      }
+      relax_batch<kHeavyBatch>(P, S, B, 0, false, ok, ee, gg, qq, C);
+    }
+  }
+}
+
 template <bool ELL>
 __device__ __forceinline__ void delta_body(const Params& P) {
   extern __shared__ __align__(16) unsigned char og_dyn_smem[];
@@ -671,6 +734,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
     if (phase == kPhRelax) relax_phase<ELL>(P, S, B, C, fused);
     else if (phase == kPhRedistMin) redist_min_phase(P);
     else if (phase == kPhRedistMove) redist_move_phase(P);
+    else if (phase == kPhBig) big_phase(P, S, B, C);
     grid_barrier(P, S, bar, phase);
   }
   const uint32_t lane = threadIdx.x & 31;
@@ -691,10 +755,10 @@ __device__ __forceinline__ void delta_body(const Params& P) {
 
 // The persistent kernel, one instantiation per adjacency layout (CSR offsets + edge
 // array for any graph; ELL-8 rows for graphs of degree at most 8).
-extern "C" __global__ void __launch_bounds__(kBlock) og_delta_kernel(Params P) {
+extern "C" __global__ void __launch_bounds__(kBlock, 3) og_delta_kernel(Params P) {
   delta_body<false>(P);
 }
-extern "C" __global__ void __launch_bounds__(kBlock) og_delta_ell_kernel(Params P) {
+extern "C" __global__ void __launch_bounds__(kBlock, 3) og_delta_ell_kernel(Params P) {
   delta_body<true>(P);
 }
 

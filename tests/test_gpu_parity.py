@@ -367,3 +367,25 @@ def test_csr_and_ell_layouts_identical(og, orc, gg, engine):
             for kind in (og.Q_PPSP, og.Q_ASTAR):
                 _, d, _ = og.query_run(G, kind, s, t, cfg=cfg)
                 assert d == orc.ppsp(g, s, t)
+
+
+def test_hub_vertices_split_across_ctas(og, orc, gg):
+    """Vertices with >= 32768 out-edges are listed and expanded by all CTAs after the
+    round (the BIG phase); a batch over a graph with several such hubs stays exact."""
+    rng = np.random.default_rng(17)
+    n = 60000
+    s = [rng.integers(0, n, 120000)]
+    d = [rng.integers(0, n, 120000)]
+    for hub in (0, 7, 12345):
+        s.append(np.full(50000, hub))
+        d.append(rng.integers(0, n, 50000))
+    s, d = np.concatenate(s), np.concatenate(d)
+    w = rng.integers(1, 5000, s.size)
+    g = gg.from_edges(n, s, d, w)
+    assert np.diff(g.offsets).max() >= 32768
+    G = og.Graph.from_csr(g)
+    srcs = [0, 7, 999, 12345]
+    out, _, _ = og.batch_run(G, [(og.Q_SSSP, x, 0, 256) for x in srcs])
+    out = out.reshape(len(srcs), n)
+    for i, x in enumerate(srcs):
+        np.testing.assert_array_equal(out[i], orc.dijkstra(g, x))
