@@ -1122,9 +1122,14 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
     if (!delta_hi) delta_hi = std::max(delta_lo, default_delta(g) * 8);
     const og_config anchor = best;
     for (uint64_t d = pow2_ceil(delta_lo); d <= delta_hi; d *= 2) {
-      og_config c = anchor;
-      c.delta = (uint32_t)d;
-      consider(c);
+      // Delta and fusion interact (a narrow bucket leaves little to fuse), so each Delta
+      // is timed with the default threshold and with fusion off.
+      for (uint32_t f : {anchor.fusion_threshold, OG_FUSION_OFF}) {
+        og_config c = anchor;
+        c.delta = (uint32_t)d;
+        c.fusion_threshold = f;
+        consider(c);
+      }
     }
   }
   // Fusion threshold (Section 5.2, configBucketFusionThreshold), frontier tile, CTAs/SM.

@@ -52,6 +52,7 @@ __device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins
                                             bool ins, bool allow_local, uint32_t v,
                                             uint32_t nd, uint32_t key, uint32_t q, Cnt& C) {
   const uint32_t lane = threadIdx.x & 31;
+  if (__ballot_sync(FULL, ins) == 0u) return;  // nothing improved in this group
   int dest = 0;  // 0 none, 1 local bin, 2 ring, 3 overflow
   if (ins) {
     const uint32_t cq = S.cur[q];
@@ -297,12 +298,14 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
   }
 }
 
-// Block-wide exclusive scan of a[0..n) (n <= 2 * kBlock) in place; a[n] = total.
+// Block-wide exclusive scan of a[0..n) in place (each thread scans a run of
+// ceil(n / kBlock) consecutive elements); a[n] = total.
 __device__ void block_exscan(uint32_t* a, uint32_t n, uint32_t* wtmp) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
-  const uint32_t x0 = i0 < n ? a[i0] : 0u, x1 = i1 < n ? a[i1] : 0u;
-  const uint32_t s = x0 + x1;
+  const uint32_t per = (n + kBlock - 1) / kBlock;
+  const uint32_t lo = min(n, tid * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; ++i) s += a[i];
   uint32_t incl = s;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -324,10 +327,13 @@ __device__ void block_exscan(uint32_t* a, uint32_t n, uint32_t* wtmp) {
     if (lane < (uint32_t)kWarps) wtmp[lane] = wi - w;
   }
   __syncthreads();
-  const uint32_t ex = wtmp[warp] + incl - s;
-  if (i0 < n) a[i0] = ex;
-  if (i1 < n) a[i1] = ex + x0;
-  if (tid == kBlock - 1) a[n] = ex + s;
+  uint32_t run = wtmp[warp] + incl - s;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t x = a[i];
+    a[i] = run;
+    run += x;
+  }
+  if (tid == kBlock - 1) a[n] = run;
   __syncthreads();
 }
 
