@@ -57,6 +57,10 @@ def parse_args(argv=None):
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--delta", type=int, default=0)
     p.add_argument("--fusion", type=int, default=0)
+    p.add_argument("--tile", type=int, default=0, help="frontier tile (with --delta)")
+    p.add_argument("--hub", type=int, default=0, help="hub out-degree (with --delta)")
+    p.add_argument("--arena", type=int, default=0,
+                   help="bucket entries per query (0 = library default)")
     p.add_argument("--cpu-sources", type=int, default=2,
                    help="oracle sample size (sources) for the CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -252,7 +256,11 @@ def run_ours(args):
         lo, hi = (1 << 8, 1 << 16)
         cfg = og.autotune(G, kind, srcs, None, lo, hi)
     elif args.delta or args.fusion:
-        cfg = og.config(delta=args.delta, fusion_threshold=args.fusion)
+        cfg = og.config(delta=args.delta, fusion_threshold=args.fusion, expand_tile=args.tile,
+                        hub_degree=args.hub)
+    if args.arena:
+        cfg = cfg if cfg is not None else og.config()
+        cfg.arena_entries = args.arena
     eff = G.get_config() if cfg is None else cfg
     queries = [(kind, int(s), 0, 0) for s in srcs]
     nq = len(queries)
@@ -333,6 +341,7 @@ def run_ours(args):
                        "fusion_threshold": int(eff.fusion_threshold),
                        "precheck": int(eff.precheck) == 1,
                        "expand_tile": int(eff.expand_tile),
+                       "hub_degree": int(eff.hub_degree),
                        "blocks_per_sm": int(eff.blocks_per_sm),
                        "engine": "async" if int(eff.engine) == 2 else "rounds",
                        "l2": "inputs larger than L2 (graph %.0f MB + dist %.0f MB > 129 MB)"

@@ -63,7 +63,8 @@ typedef struct og_config {
   uint32_t fusion_threshold; /* bucket fusion: a CTA keeps draining its local bin of the
                                 current bucket while 0 < size < threshold (Section 3.3);
                                 OG_FUSION_OFF disables fusion, 0xFFFFFFFF = unbounded   */
-  uint32_t expand_tile;      /* frontier entries a CTA claims per grab (multiple of 32) */
+  uint32_t expand_tile;      /* frontier entries a CTA claims per grab (multiple of 32;
+                                0 = 32 for average degree <= 8, else 256)              */
   uint32_t blocks_per_sm;    /* persistent CTAs per SM (capped by occupancy)           */
   uint32_t ring_buckets;     /* materialised buckets (power of two, <= 256); further
                                 buckets go to one overflow pile (Section 5.1's lazy
@@ -78,7 +79,11 @@ typedef struct og_config {
                                 0 = CSR)                                               */
   uint32_t prefetch;         /* OG_PREFETCH_ON / _OFF: prefetch an inserted vertex's
                                 adjacency into L2 (0 = off)                           */
-  uint32_t reserved1;
+  uint32_t hub_degree;       /* out-degree from which a frontier vertex is a hub: instead
+                                of being expanded by the CTA that meets it, its edges
+                                are split over every warp of the grid in a pass after
+                                the round (round engine, CSR layout; 0 = default 4096,
+                                0xFFFFFFFF = no hubs)                                  */
   uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
   uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
 } og_config;
@@ -120,7 +125,8 @@ typedef struct og_stats {
   uint64_t flushes;          /* local buckets copied to a global bucket (fusion limit) */
   uint64_t t_frontier_ns;    /* round engine, summed over CTAs: frontier passes,       */
   uint64_t t_fused_ns;       /*   fused-round loops,                                   */
-  uint64_t t_barrier_ns;     /*   and grid-barrier waits                               */
+  uint64_t t_barrier_ns;     /*   grid-barrier waits,                                  */
+  uint64_t t_hub_ns;         /*   and hub passes (BIG phase)                           */
 } og_stats;
 
 typedef struct og_query {

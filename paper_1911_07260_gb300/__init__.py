@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
                 ("expand_tile", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("ring_buckets", ctypes.c_uint32), ("engine", ctypes.c_uint32),
                 ("precheck", ctypes.c_uint32), ("layout", ctypes.c_uint32),
-                ("prefetch", ctypes.c_uint32), ("reserved1", ctypes.c_uint32),
+                ("prefetch", ctypes.c_uint32), ("hub_degree", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("arena_entries", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
                 ("rounds", "fused_iters", "items", "stale", "relax", "improved",
                  "local_inserts", "global_inserts", "overflow_inserts", "redistributions",
                  "restarts", "kernel_ns", "flushes", "t_frontier_ns", "t_fused_ns",
-                 "t_barrier_ns")]
+                 "t_barrier_ns", "t_hub_ns")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

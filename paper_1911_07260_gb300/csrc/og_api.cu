@@ -106,7 +106,7 @@ struct HBuf {
 
 // Device scratch of one launch configuration (grown on demand, reused across calls).
 struct Workspace {
-  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big;
+  DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big, bmap;
   HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // Barrier-free engine: ring positions must read "free" (all ones) before use.  Entries
@@ -116,7 +116,7 @@ struct Workspace {
   void* ring_ptr = nullptr;
   void release() {
     for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
-                    &big})
+                    &big, &bmap})
       b->release();
     for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq}) b->release();
     clean_upto = 0;
@@ -158,8 +158,12 @@ uint32_t pow2_ceil(uint64_t x) {
 
 constexpr uint32_t kDefaultFusion = 1024;
 constexpr int kEllWidthHost = 8;
-constexpr uint32_t kDefaultTile = 128;
+constexpr uint32_t kTileSparse = 32;    // frontier tile, average degree <= 8
+constexpr uint32_t kTileDense = 256;    // frontier tile, denser graphs
 constexpr uint32_t kBinCap = 2048;
+constexpr uint32_t kDefaultHub = 4096;      // out-degree from which a vertex is a hub
+constexpr uint32_t kHubSlots = 65536;       // hubs listed per round
+constexpr uint32_t kHubChunks = 1u << 20;   // 1024-edge hub chunks per round
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 
 }  // namespace
@@ -222,9 +226,14 @@ og_config resolve(const og_graph* g, const og_config* user) {
   const og_config& u = user ? *user : z;
   r.delta = pick32(u.delta, g->cfg.delta, default_delta(g));
   r.fusion_threshold = pick32(u.fusion_threshold, g->cfg.fusion_threshold, kDefaultFusion);
-  r.expand_tile = pick32(u.expand_tile, g->cfg.expand_tile, kDefaultTile);
+  // Sparse graphs: small tiles spread a narrow frontier over many CTAs, whose fused loops
+  // then carry the work; dense graphs: a tile of one entry per thread amortises the
+  // claim and the degree scan of the CTA-wide expansion.
+  const uint32_t tile = (g->n && (double)g->m / g->n > 8.0) ? kTileDense : kTileSparse;
+  r.expand_tile = pick32(u.expand_tile, g->cfg.expand_tile, tile);
   r.blocks_per_sm = pick32(u.blocks_per_sm, g->cfg.blocks_per_sm, 0);
   r.ring_buckets = pick32(u.ring_buckets, g->cfg.ring_buckets, 0);
+  r.hub_degree = pick32(u.hub_degree, g->cfg.hub_degree, kDefaultHub);
   r.spin_limit_ns = pick64(u.spin_limit_ns, g->cfg.spin_limit_ns, kDefaultSpinNs);
   r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
   r.engine = u.engine ? u.engine : g->cfg.engine;
@@ -329,8 +338,11 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     TRY(ws.slots.ensure(sizeof(uint32_t) * nq));
     TRY(ws.h_slots.ensure(sizeof(uint32_t) * nq));
     memcpy(ws.h_slots.p, pending.data(), sizeof(uint32_t) * np);
-    const uint32_t big_cap = g->max_deg >= kBigDegree ? 65536u : 0u;
-    if (big_cap) TRY(ws.big.ensure(sizeof(BigItem) * big_cap));
+    const uint32_t big_cap = g->max_deg >= c.hub_degree ? kHubSlots : 0u;
+    if (big_cap) {
+      TRY(ws.big.ensure(sizeof(BigItem) * big_cap));
+      TRY(ws.bmap.ensure(sizeof(uint32_t) * kHubChunks));
+    }
 
     Params P{};
     P.off = g->off;
@@ -349,7 +361,10 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     P.sync = ws.sync.as<Sync>();
     P.stats = ws.stats.as<Stats>();
     P.big = big_cap ? ws.big.as<BigItem>() : nullptr;
+    P.big_map = big_cap ? ws.bmap.as<uint32_t>() : nullptr;
     P.big_cap = big_cap;
+    P.map_cap = big_cap ? kHubChunks : 0u;
+    P.hub_min = c.hub_degree;
     P.nq = nq;
     P.B = B;
     P.Bmask = B - 1;
@@ -610,6 +625,7 @@ void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
   out->t_frontier_ns = s.v[kStTFrontier];
   out->t_fused_ns = s.v[kStTFused];
   out->t_barrier_ns = s.v[kStTBarrier];
+  out->t_hub_ns = s.v[kStTHub];
 }
 
 int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d) {
@@ -705,7 +721,7 @@ void og_config_default(og_config* c) {
   if (!c) return;
   memset(c, 0, sizeof(*c));
   c->fusion_threshold = kDefaultFusion;
-  c->expand_tile = kDefaultTile;
+  c->hub_degree = kDefaultHub;
   c->spin_limit_ns = kDefaultSpinNs;
 }
 
@@ -1159,6 +1175,13 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
     og_config c = best;
     c.expand_tile = t;
     consider(c);
+  }
+  if (g->max_deg >= 1024) {  // skewed degrees: where hubs go to the grid-wide pass
+    for (uint32_t h : {1024u, 4096u, 32768u, 0xFFFFFFFFu}) {
+      og_config c = best;
+      c.hub_degree = h;
+      consider(c);
+    }
   }
   for (uint32_t b = 1; b <= (uint32_t)std::max(1, g->occ); ++b) {
     og_config c = best;

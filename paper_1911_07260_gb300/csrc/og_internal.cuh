@@ -35,13 +35,15 @@ enum Phase : uint32_t {
   kPhBig = 5,        // edges of very-high-degree vertices, split over all CTAs
 };
 
-// A vertex whose out-degree is at least kBigDegree (a hub of a skewed graph) is not
-// expanded by one warp: it is listed, and after the round every CTA claims 1024-edge
-// chunks of it.
-constexpr uint32_t kBigDegree = 32768;
+// A vertex whose out-degree is at least Params::hub_min (a hub of a skewed graph) is not
+// expanded by the CTA that meets it: it is listed, and after the round every warp of the
+// grid claims kBigSub-edge pieces of the listed hubs.  Each hub owns a contiguous range of
+// kBigChunk-edge chunks; the chunk map names the hub of every chunk.
 constexpr uint32_t kBigChunk = 1024;
+constexpr uint32_t kBigSub = 256;                  // edges per warp claim
+constexpr uint32_t kBigSubs = kBigChunk / kBigSub;  // claims per chunk
 struct BigItem {
-  uint32_t u, g, q, beg, end, next;
+  uint32_t u, g, q, beg, end, cbase;  // cbase: first chunk of this hub
 };
 
 enum ErrBits : uint32_t { kErrTimeout = 1, kErrArena = 2, kErrSat = 4, kErrBounds = 8 };
@@ -80,19 +82,20 @@ struct Sync {
   uint32_t rounds;       // rounds run in this launch
   uint32_t any_active;
   uint32_t active;       // barrier-free engine: queries not yet finished
-  uint32_t big_n;        // listed very-high-degree vertices (round engine)
+  uint32_t big_claim;    // hub pieces claimed in the BIG phase (round engine)
   uint32_t bad_code;     // first failed internal bounds check (0 = none)
   uint32_t bad_val;      // the offending value
   uint32_t bad_aux;      // context (query or position)
   uint32_t progress;     // barrier-free engine: heartbeat of busy warps
   uint32_t timeout_at;   // which bounded wait gave up (1 idle, 2 entry hand-off)
   uint32_t pad[1];
+  unsigned long long big_word;  // (listed hubs << 32) | chunks reserved, this round
 };
 
 enum StatIdx {
   kStRounds, kStFused, kStItems, kStStale, kStRelax, kStImproved, kStLocal, kStGlobal,
   kStOvf, kStRedist, kStFlush,
-  kStTFrontier, kStTFused, kStTBarrier,  // ns summed over CTAs (round engine)
+  kStTFrontier, kStTFused, kStTBarrier, kStTHub,  // ns summed over CTAs (round engine)
   kStCount
 };
 struct Stats { unsigned long long v[16]; };
@@ -114,8 +117,11 @@ struct Params {
   uint32_t* fr_pref;      // nq + 1 prefix sums of the frontier sizes
   Sync* sync;
   Stats* stats;
-  BigItem* big;           // very-high-degree vertices of the current round (or null)
-  uint32_t big_cap;
+  BigItem* big;           // hubs listed in the current round (or null: no hub list)
+  uint32_t* big_map;      // chunk -> hub slot (kNone: chunk of a hub that did not fit)
+  uint32_t big_cap;       // hub slots
+  uint32_t map_cap;       // chunk map entries
+  uint32_t hub_min;       // out-degree from which a vertex is listed as a hub
   uint32_t nq;
   uint32_t B, Bmask;
   uint32_t cap;           // entries per ring slot

@@ -32,7 +32,9 @@ struct Smem {
   uint32_t err;
   uint32_t f_active, f_redist;
   uint32_t wtmp[kWarps + 1];
-  unsigned long long t_front, t_fused, t_bar;  // per-CTA phase time (thread 0)
+  uint32_t lb_pos[kBlock + 1];  // CTA-wide expansion: edge prefix sums of the entries
+  uint32_t lb_beg[kBlock], lb_g[kBlock], lb_q[kBlock];
+  unsigned long long t_front, t_fused, t_bar, t_hub;  // per-CTA phase time (thread 0)
 };
 
 struct Bins {
@@ -180,6 +182,32 @@ __device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins
 constexpr int kLightBatch = 4;  // light-edge groups of 32 relaxed per batch
 constexpr int kHeavyBatch = 4;  // groups of 32 edges of one heavy vertex per batch
 
+// Lists a hub for the BIG phase.  One 64-bit atomicAdd reserves the hub's slot (high
+// word) and its range of kBigChunk-edge chunks (low word) together, so chunk ranges grow
+// with the slot; the chunk map then names the slot of each of its chunks.  Returns false
+// when the list or the map is full: the caller expands the vertex itself, and the chunks
+// it reserved are marked kNone.
+__device__ __noinline__ bool push_hub(const Params& P, uint32_t u, uint32_t g, uint32_t q,
+                                      uint32_t beg, uint32_t end) {
+  const uint32_t nch = (end - beg + kBigChunk - 1) / kBigChunk;
+  const unsigned long long w = atomicAdd(&P.sync->big_word, (1ull << 32) | nch);
+  const uint32_t slot = (uint32_t)(w >> 32), cbase = (uint32_t)w;
+  const bool fits = slot < P.big_cap && cbase <= P.map_cap && nch <= P.map_cap - cbase;
+  if (fits) {
+    BigItem it;
+    it.u = u;
+    it.g = g;
+    it.q = q;
+    it.beg = beg;
+    it.end = end;
+    it.cbase = cbase;
+    P.big[slot] = it;
+  }
+  const uint32_t lim = cbase < P.map_cap ? min(P.map_cap - cbase, nch) : 0u;
+  for (uint32_t c = 0; c < lim; ++c) P.big_map[cbase + c] = fits ? slot : kNone;
+  return fits;
+}
+
 // Expands the bucket entries held by a warp (one per lane with has): drops entries whose
 // vertex has a smaller distance by now (a newer entry exists), then relaxes all out-edges.
 // Vertices with >= 32 edges are expanded by the whole warp one at a time; the others are
@@ -231,22 +259,7 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
       beg = end = 0;
     }
   }
-  const uint32_t deg = end - beg;
-  if (deg >= kBigDegree && P.big) {
-    // Hub: list it; all CTAs split its edges after the round.
-    const uint32_t slot = atomicAdd(&P.sync->big_n, 1u);
-    if (slot < P.big_cap) {
-      BigItem it;
-      it.u = u;
-      it.g = g;
-      it.q = q;
-      it.beg = beg;
-      it.end = end;
-      it.next = 0;
-      P.big[slot] = it;
-      beg = end = 0;
-    }
-  }
+  if (end - beg >= P.hub_min && P.big && push_hub(P, u, g, q, beg, end)) beg = end = 0;
   const bool heavy = end - beg >= 32u;
   unsigned hm = __ballot_sync(FULL, heavy);
   while (hm) {
@@ -337,6 +350,58 @@ __device__ void block_exscan(uint32_t* a, uint32_t n, uint32_t* wtmp) {
   __syncthreads();
 }
 
+// Expands up to kBlock bucket entries (one per thread with has) with the whole CTA: after
+// the stale check the entries' out-degrees are scanned, and all threads walk the joined
+// edge list together, edge idx going to the entry whose range holds it (binary search in
+// shared memory).  Thread t of a batch takes edge e0 + t, so a warp reads 32 consecutive
+// edges and one high-degree entry no longer holds up a single warp.  Hubs are listed for
+// the BIG phase instead.  Must be called by all threads of the CTA (CSR layout only).
+__device__ __forceinline__ void expand_cta(const Params& P, Smem& S, const Bins& B, int out,
+                                           bool allow_local, bool has, uint32_t u,
+                                           uint32_t g, uint32_t q, Cnt& C) {
+  const uint32_t tid = threadIdx.x;
+  uint32_t beg = 0, deg = 0;
+  if (has) {
+    C.items++;
+    const uint32_t d = __ldcg(P.dist + (size_t)q * P.n + u);
+    beg = __ldg(P.off + u);
+    const uint32_t end = __ldg(P.off + u + 1);
+    if (d != g) {
+      C.stale++;
+    } else {
+      deg = end - beg;
+      if (deg >= P.hub_min && P.big && push_hub(P, u, g, q, beg, end)) deg = 0;
+    }
+  }
+  S.lb_pos[tid] = deg;
+  S.lb_beg[tid] = beg;
+  S.lb_g[tid] = g;
+  S.lb_q[tid] = q;
+  __syncthreads();
+  block_exscan(S.lb_pos, kBlock, S.wtmp);
+  const uint32_t total = S.lb_pos[kBlock];
+  for (uint32_t e0 = 0; e0 < total; e0 += kBlock * kLightBatch) {
+    bool ok[kLightBatch];
+    uint32_t ee[kLightBatch], gg[kLightBatch], qq[kLightBatch];
+#pragma unroll
+    for (int k = 0; k < kLightBatch; ++k) {
+      const uint32_t idx = e0 + (uint32_t)k * kBlock + tid;
+      ok[k] = idx < total;
+      uint32_t j = 0;  // last entry whose edge range starts at or before idx
+      if (ok[k]) {
+#pragma unroll
+        for (uint32_t s = kBlock / 2; s > 0; s >>= 1)
+          if (S.lb_pos[j + s] <= idx) j += s;
+      }
+      ee[k] = S.lb_beg[j] + (idx - S.lb_pos[j]);
+      gg[k] = S.lb_g[j];
+      qq[k] = S.lb_q[j];
+    }
+    relax_batch<kLightBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
+  }
+  __syncthreads();  // the lb arrays are refilled by the next call
+}
+
 // Run by the CTA that arrives last at a grid barrier, before it releases the others:
 // advances every query's bucket cursor and publishes the next phase and frontier.
 __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
@@ -344,7 +409,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
   Sync* sy = P.sync;
   const uint32_t err = ld_relaxed(&sy->err);
   const bool fatal = (err & kErrFatal) != 0;
-  if (done_phase == kPhRelax && !fatal && __ldcg(&sy->big_n) > 0u) {
+  if (done_phase == kPhRelax && !fatal && (__ldcg(&sy->big_word) >> 32) > 0u) {
     // Listed hubs first: the same round continues with the BIG phase.
     if (tid == 0) {
       sy->phase = kPhBig;
@@ -353,7 +418,10 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
     return;
   }
   if (done_phase == kPhBig) {
-    if (tid == 0) sy->big_n = 0;
+    if (tid == 0) {
+      sy->big_word = 0ull;
+      sy->big_claim = 0u;
+    }
     done_phase = kPhRelax;
   }
   if (tid == 0) {
@@ -550,9 +618,10 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
     const uint32_t base = S.grab;
     __syncthreads();
     if (base >= total) break;
-    for (uint32_t k = tid; k < P.tile; k += kBlock) {
+    for (uint32_t k = tid; k < (ELL ? P.tile : (P.tile + kBlock - 1) / kBlock * kBlock);
+         k += kBlock) {
       const uint32_t i = base + k;
-      const bool has = i < total;
+      const bool has = k < P.tile && i < total;
       uint32_t u = 0, g = 0, q = 0;
       if (has) {
         uint32_t lo = 0, hi = P.nq;
@@ -567,7 +636,8 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
         u = en.x;
         g = en.y;
       }
-      expand_warp<ELL>(P, S, B, 0, fuse, has, u, g, q, C);
+      if constexpr (ELL) expand_warp<true>(P, S, B, 0, fuse, has, u, g, q, C);
+      else expand_cta(P, S, B, 0, fuse, has, u, g, q, C);
     }
   }
   const uint64_t t_mid = tid == 0 ? gtimer() : 0ull;
@@ -683,40 +753,42 @@ __device__ void redist_move_phase(const Params& P) {
   }
 }
 
-// The BIG phase: every CTA walks the list of hubs of this round and claims 1024-edge
-// chunks of each (8 warps x 4 groups of 32 edges), so one hub no longer holds up a round.
-// Improved vertices go to the global buckets.
+// The BIG phase: the warps of all CTAs claim kBigSub-edge pieces of the hubs listed in
+// this round (one counter; piece c lies in chunk c / kBigSubs, whose hub the chunk map
+// names), so a hub is spread over the whole grid.  Improved vertices go to the global
+// buckets.
 __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint64_t t_start = tid == 0 ? gtimer() : 0ull;
   for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
   __syncthreads();
-  const uint32_t n = min(__ldcg(&P.sync->big_n), P.big_cap);
-  for (uint32_t i = 0; i < n; ++i) {
-    BigItem* it = P.big + i;
+  const uint32_t nsub = min((uint32_t)__ldcg(&P.sync->big_word), P.map_cap) * kBigSubs;
+  for (;;) {
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(&P.sync->big_claim, 1u);
+    c = __shfl_sync(FULL, c, 0);
+    if (c >= nsub) break;
+    const uint32_t slot = __ldcg(P.big_map + c / kBigSubs);
+    if (slot >= P.big_cap) continue;  // chunk of a hub that did not fit (expanded in place)
+    const BigItem* it = P.big + slot;
     const uint32_t hb = __ldcg(&it->beg), he = __ldcg(&it->end);
-    const uint32_t hg = __ldcg(&it->g), hq = __ldcg(&it->q);
-    for (;;) {
-      if (tid == 0) {
-        // one read skips a hub whose edges are all claimed already
-        S.grab = __ldcg(&it->next) >= he - hb ? he - hb : atomicAdd(&it->next, kBigChunk);
-      }
-      __syncthreads();
-      const uint32_t c = S.grab;
-      __syncthreads();
-      if (c >= he - hb) break;
-      const uint32_t e0 = hb + c + warp * (kBigChunk / kWarps);
+    const uint32_t hg = __ldcg(&it->g), hq = __ldcg(&it->q), cb = __ldcg(&it->cbase);
+    const uint32_t e0 = hb + (c / kBigSubs - cb) * kBigChunk + (c % kBigSubs) * kBigSub;
+    for (uint32_t s0 = e0; s0 < min(he, e0 + kBigSub); s0 += 32 * kHeavyBatch) {
       bool ok[kHeavyBatch];
       uint32_t ee[kHeavyBatch], gg[kHeavyBatch], qq[kHeavyBatch];
 #pragma unroll
       for (int k = 0; k < kHeavyBatch; ++k) {
-        ee[k] = e0 + 32u * k + lane;
-        ok[k] = ee[k] < he && ee[k] < hb + c + kBigChunk;
+        ee[k] = s0 + 32u * k + lane;
+        ok[k] = ee[k] < he;
         gg[k] = hg;
         qq[k] = hq;
       }
       relax_batch<kHeavyBatch>(P, S, B, 0, false, ok, ee, gg, qq, C);
     }
   }
+  __syncthreads();
+  if (tid == 0) S.t_hub += gtimer() - t_start;
 }
 
 template <bool ELL>
@@ -732,7 +804,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
   Cnt C = {0, 0, 0, 0, 0, 0, 0};
   uint32_t fused = 0;
   uint32_t bar = 0;
-  if (threadIdx.x == 0) S.t_front = S.t_fused = S.t_bar = 0ull;
+  if (threadIdx.x == 0) S.t_front = S.t_fused = S.t_bar = S.t_hub = 0ull;
   grid_barrier(P, S, bar, kPhPrologue);
   for (;;) {
     const uint32_t phase = S.phase;
@@ -740,7 +812,9 @@ __device__ __forceinline__ void delta_body(const Params& P) {
     if (phase == kPhRelax) relax_phase<ELL>(P, S, B, C, fused);
     else if (phase == kPhRedistMin) redist_min_phase(P);
     else if (phase == kPhRedistMove) redist_move_phase(P);
-    else if (phase == kPhBig) big_phase(P, S, B, C);
+    else if (phase == kPhBig) {
+      if constexpr (!ELL) big_phase(P, S, B, C);  // ELL rows hold <= 8 edges: no hubs
+    }
     grid_barrier(P, S, bar, phase);
   }
   const uint32_t lane = threadIdx.x & 31;
@@ -756,6 +830,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
     atomicAdd(&P.stats->v[kStTFrontier], S.t_front);
     atomicAdd(&P.stats->v[kStTFused], S.t_fused);
     atomicAdd(&P.stats->v[kStTBarrier], S.t_bar);
+    atomicAdd(&P.stats->v[kStTHub], S.t_hub);
   }
 }
 

@@ -370,8 +370,9 @@ def test_csr_and_ell_layouts_identical(og, orc, gg, engine):
 
 
 def test_hub_vertices_split_across_ctas(og, orc, gg):
-    """Vertices with >= 32768 out-edges are listed and expanded by all CTAs after the
-    round (the BIG phase); a batch over a graph with several such hubs stays exact."""
+    """Vertices with >= hub_degree out-edges (default 4096) are listed and expanded by all
+    warps after the round (the BIG phase); a batch over a graph with several such hubs
+    stays exact."""
     rng = np.random.default_rng(17)
     n = 60000
     s = [rng.integers(0, n, 120000)]
@@ -389,3 +390,21 @@ def test_hub_vertices_split_across_ctas(og, orc, gg):
     out = out.reshape(len(srcs), n)
     for i, x in enumerate(srcs):
         np.testing.assert_array_equal(out[i], orc.dijkstra(g, x))
+
+
+@pytest.mark.parametrize("hub", [32, 200, 1024, 0xFFFFFFFF])
+@pytest.mark.parametrize("fusion", [1024, 0xFFFFFFFE])
+def test_hub_degree_sweep_rmat(og, orc, gg, hub, fusion):
+    """The hub threshold only moves work between the CTA that meets a vertex and the BIG
+    phase: every threshold (down to 32, where most edges of an R-MAT graph belong to hubs,
+    up to none) and fusion on or off give the oracle's distances for a 4-query batch."""
+    g = gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 1 << 16, seed=5)
+    G = og.Graph.from_csr(g)
+    srcs = [int(x) for x in gg.sample_sources(g, 4, seed=3)]
+    for tile in (32, 384):
+        cfg = og.config(engine=og.ENGINE_ROUNDS, hub_degree=hub, fusion_threshold=fusion,
+                        expand_tile=tile)
+        out, _, _ = og.batch_run(G, [(og.Q_SSSP, x, 0, 512) for x in srcs], cfg=cfg)
+        out = out.reshape(len(srcs), g.n)
+        for i, x in enumerate(srcs):
+            np.testing.assert_array_equal(out[i], orc.dijkstra(g, x))
