@@ -405,6 +405,11 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     const Sync* hy = ws.h_sync.as<Sync>();
     const QState* hq = ws.h_qs.as<QState>();
     ro->err |= hy->err & ~(uint32_t)kErrArena;
+    if (hy->err & kErrBounds) {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
+               hy->bad_code, hy->bad_val, hy->bad_aux);
+      return OG_E_INTERNAL;
+    }
     if (hy->err & kErrTimeout) {
       snprintf(g_cuda_msg, sizeof(g_cuda_msg), "grid barrier wait gave up");
       return OG_E_TIMEOUT;
