@@ -441,9 +441,10 @@ def run_batch(args):
     G = og.Graph.from_csr(g)
     srcs = graphgen.sample_sources(g, 128, seed=2)
     pairs = graphgen.sample_pairs_grid_steps(g, 128, 10, 1000, seed=2)
-    cfg = og.autotune(G, og.Q_SSSP, srcs[:8], None, 1 << 8, 1 << 16)
     queries = [(og.Q_SSSP, int(s), 0, 0) for s in srcs] + \
               [(og.Q_PPSP, int(a), int(b), 0) for a, b in pairs]
+    cfg = og.autotune_batch(G, queries, 1 << 8, 1 << 16)  # tuned on the batch itself
+    cfg1 = og.autotune(G, og.Q_SSSP, srcs[:1], None, 1 << 8, 1 << 16)  # and on one query
     nq = len(queries)
     dbuf = torch.empty(nq * g.n, dtype=torch.int32, device="cuda")
     _, d_batch, _ = og.batch_run(G, queries, cfg=cfg, out=dbuf)
@@ -469,7 +470,7 @@ def run_batch(args):
     t0 = time.perf_counter()
     exact = True
     for i, (kind, s, t, _) in enumerate(queries):
-        out, d, _ = og.query_run(G, kind, s, t, 0, cfg=cfg, out=one if kind == og.Q_SSSP else None)
+        out, d, _ = og.query_run(G, kind, s, t, 0, cfg=cfg1, out=one if kind == og.Q_SSSP else None)
         if kind == og.Q_SSSP:
             exact &= bool(np.array_equal(one.cpu().numpy().view(np.uint32), dist_b[i]))
         else:
@@ -497,8 +498,12 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": "road-like 1024x1024 grid, 256 queries in one persistent launch",
                    "n": g.n, "m": g.m, "delta": int(cfg.delta),
-                   "fusion_threshold": int(cfg.fusion_threshold), "engine": int(cfg.engine)},
+                   "fusion_threshold": int(cfg.fusion_threshold),
+                   "expand_tile": int(cfg.expand_tile), "engine": int(cfg.engine)},
         "one_at_a_time": {"value": round(nq / single_s, 2), "unit": "queries/s",
+                          "schedule": {"delta": int(cfg1.delta),
+                                       "fusion_threshold": int(cfg1.fusion_threshold),
+                                       "expand_tile": int(cfg1.expand_tile)},
                           "speedup_batched": round(single_s / batch_s, 2)},
         "exact_batched_eq_alone_eq_oracle": exact,
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),

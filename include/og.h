@@ -233,6 +233,15 @@ void og_server_free(og_server* s);
 int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t* dsts,
                 uint32_t nsample, uint32_t delta_lo, uint32_t delta_hi, og_config* out);
 
+/* The same search timed on a whole batch: queries (host array of nq, mixed kinds allowed;
+ * a query's delta field should be 0 so that each candidate's Delta applies) run together
+ * in the launches of og_batch_run under each candidate.  A batch needs its own schedule:
+ * its CTA-local bins hold entries of many queries at once, so the best fusion threshold
+ * and tile differ from those of one query.  Stores the winner as the graph default and
+ * in *out.  OG_E_INVALID for an empty batch, a bad kind or a vertex id >= n. */
+int og_autotune_batch(og_graph* g, const og_query* queries, uint32_t nq, uint32_t delta_lo,
+                      uint32_t delta_hi, og_config* out);
+
 /* ---- allocation-free variant -----------------------------------------------------------
  * og_sssp_delta_noalloc: the same Delta-stepping SSSP as og_sssp_delta for callers that
  * cannot allocate device memory -- code inside a host application whose allocator has

@@ -99,6 +99,7 @@ def lib():
             "og_server_slots": (i32, [vp, P(u32), P(u32)]),
             "og_server_free": (None, [vp]),
             "og_autotune": (i32, [vp, u32, vp, vp, u32, u32, u32, P(Config)]),
+            "og_autotune_batch": (i32, [vp, vp, u32, u32, u32, P(Config)]),
             "og_strerror": (ctypes.c_char_p, [i32]),
             "og_last_cuda_error": (ctypes.c_char_p, []),
             "og_version": (i32, []),
@@ -354,6 +355,16 @@ def autotune(g: Graph, kind: int, srcs, dsts=None, delta_lo: int = 0, delta_hi: 
     c = Config()
     _check(lib().og_autotune(g.handle, kind, srcs.ctypes.data, None if dd is None else dd.ctypes.data,
                              srcs.shape[0], delta_lo, delta_hi, ctypes.byref(c)), "og_autotune")
+    return c
+
+
+def autotune_batch(g: Graph, queries, delta_lo: int = 0, delta_hi: int = 0) -> Config:
+    """Tunes the schedule on a whole batch [(kind, src, dst, delta), ...]."""
+    nq = len(queries)
+    arr = (Query * nq)(*[Query(*map(int, q)) for q in queries])
+    c = Config()
+    _check(lib().og_autotune_batch(g.handle, arr, nq, delta_lo, delta_hi, ctypes.byref(c)),
+           "og_autotune_batch")
     return c
 
 

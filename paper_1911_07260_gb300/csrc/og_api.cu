@@ -1108,13 +1108,14 @@ void og_server_free(og_server* s) {
 
 // ---- autotuning ---------------------------------------------------------------------------
 
-int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t* dsts,
-                uint32_t nsample, uint32_t delta_lo, uint32_t delta_hi, og_config* out) {
-  if (!g || !srcs || nsample == 0 || kind > OG_Q_WBFS) return OG_E_INVALID;
-  if ((kind == OG_Q_PPSP || kind == OG_Q_ASTAR) && !dsts) return OG_E_INVALID;
-  std::vector<og_query> qs(nsample);
-  for (uint32_t i = 0; i < nsample; ++i)
-    qs[i] = og_query{kind, srcs[i], dsts ? dsts[i] : 0u, 0u};
+namespace {
+
+// Coordinate search over the schedule, timing the queries qs in one launch per candidate.
+int autotune_queries(og_graph* g, const std::vector<og_query>& qs, uint32_t delta_lo,
+                     uint32_t delta_hi, og_config* out) {
+  const uint32_t nsample = (uint32_t)qs.size();
+  bool all_wbfs = true;
+  for (const og_query& q : qs) all_wbfs &= q.kind == OG_Q_WBFS;
   og_config base = resolve(g, nullptr);
   base.engine = OG_ENGINE_ROUNDS;
   // One candidate: a warm-up run, then the device time of a second run.  A candidate
@@ -1138,7 +1139,7 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
     }
   };
   // Delta (Section 6.2: the best coarsening factor depends on the graph), with fusion on.
-  if (kind != OG_Q_WBFS) {
+  if (!all_wbfs) {
     if (!delta_lo) delta_lo = std::max(1u, default_delta(g) / 64);
     if (!delta_hi) delta_hi = std::max(delta_lo, default_delta(g) * 8);
     const og_config anchor = best;
@@ -1204,6 +1205,29 @@ int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t
   g->cfg = best;
   if (out) *out = best;
   return OG_OK;
+}
+
+}  // namespace
+
+int og_autotune(og_graph* g, uint32_t kind, const uint32_t* srcs, const uint32_t* dsts,
+                uint32_t nsample, uint32_t delta_lo, uint32_t delta_hi, og_config* out) {
+  if (!g || !srcs || nsample == 0 || kind > OG_Q_WBFS) return OG_E_INVALID;
+  if ((kind == OG_Q_PPSP || kind == OG_Q_ASTAR) && !dsts) return OG_E_INVALID;
+  std::vector<og_query> qs(nsample);
+  for (uint32_t i = 0; i < nsample; ++i)
+    qs[i] = og_query{kind, srcs[i], dsts ? dsts[i] : 0u, 0u};
+  return autotune_queries(g, qs, delta_lo, delta_hi, out);
+}
+
+int og_autotune_batch(og_graph* g, const og_query* queries, uint32_t nq, uint32_t delta_lo,
+                      uint32_t delta_hi, og_config* out) {
+  if (!g || !queries || nq == 0) return OG_E_INVALID;
+  std::vector<og_query> qs(queries, queries + nq);
+  for (const og_query& q : qs)
+    if (q.kind > OG_Q_WBFS || q.src >= g->n ||
+        ((q.kind == OG_Q_PPSP || q.kind == OG_Q_ASTAR) && q.dst >= g->n))
+      return OG_E_INVALID;
+  return autotune_queries(g, qs, delta_lo, delta_hi, out);
 }
 
 }  // extern "C"

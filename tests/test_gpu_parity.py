@@ -408,3 +408,25 @@ def test_hub_degree_sweep_rmat(og, orc, gg, hub, fusion):
         out = out.reshape(len(srcs), g.n)
         for i, x in enumerate(srcs):
             np.testing.assert_array_equal(out[i], orc.dijkstra(g, x))
+
+
+def test_autotune_batch_mixed_queries(og, orc, gg, road300):
+    """The batch tuner times a mixed SSSP / PPSP / A* batch under its candidates; the
+    schedule it returns keeps every query exact.  Bad arguments are rejected."""
+    g, G = road300
+    srcs = [int(x) for x in gg.sample_sources(g, 6, seed=11)]
+    qs = [(og.Q_SSSP, srcs[0], 0, 0), (og.Q_SSSP, srcs[1], 0, 0),
+          (og.Q_PPSP, srcs[2], srcs[3], 0), (og.Q_ASTAR, srcs[4], srcs[5], 0)]
+    cfg = og.autotune_batch(G, qs, 1 << 8, 1 << 14)
+    assert cfg.delta >= 1 and cfg.fusion_threshold > 0
+    out, d, _ = og.batch_run(G, qs, cfg=cfg)
+    out = out.reshape(len(qs), g.n)
+    np.testing.assert_array_equal(out[0], orc.dijkstra(g, srcs[0]))
+    np.testing.assert_array_equal(out[1], orc.dijkstra(g, srcs[1]))
+    assert d[2] == orc.ppsp(g, srcs[2], srcs[3])
+    assert d[3] == orc.ppsp(g, srcs[4], srcs[5])
+    for bad in ([], [(og.Q_SSSP, g.n, 0, 0)], [(7, 0, 0, 0)], [(og.Q_PPSP, 0, g.n, 0)]):
+        with pytest.raises(og.OgError) as e:
+            og.autotune_batch(G, bad)
+        assert e.value.code == og.E_INVALID
+    G.set_config(og.Config())  # the fixture's graph goes back to library defaults
