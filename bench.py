@@ -16,7 +16,9 @@ The graph (760 MB) and the distance arrays (8 x 96 MB) exceed the 129 MB L2, so 
 flush is needed between steps.
 
 Other workloads (--workload): rmat-wbfs, rmat-sssp (R-MAT scale 24), batch (256 queries
-on a 1024 x 1024 road-like grid, queries/s), serve (Poisson A*/PPSP stream, p50/p99).
+on a 1024 x 1024 road-like grid, queries/s), serve (Poisson A*/PPSP stream, p50/p99),
+road-bf (the default graph and sources by the unordered Bellman-Ford baseline, with the
+ordered method's time on the same sources for the comparison of Section 6).
 
 --impl reference times the CPU oracle (single-threaded Dijkstra) on the same workload
 and metric, one bounded sample per step.
@@ -50,7 +52,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="road-sssp",
-                   choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve"])
+                   choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf"])
     p.add_argument("--side", type=int, default=4900, help="road-like grid side")
     p.add_argument("--scale", type=int, default=24, help="R-MAT scale")
     p.add_argument("--sources", type=int, default=8)
@@ -219,7 +221,7 @@ def algo_bytes(m_r: int, n_r: int, n: int) -> int:
 
 def build_workload(args, rank, world):
     import graphgen
-    if args.workload in ("road-sssp", "serve"):
+    if args.workload in ("road-sssp", "serve", "road-bf"):
         side = args.side
         g = graphgen.road(side, 0.15, 0.02, seed=1)
         name = f"road-like {side}x{side} grid"
@@ -250,7 +252,7 @@ def run_ours(args):
 
     g, gname, srcs = build_workload(args, rank, world)
     G = og.Graph.from_csr(g)
-    kind = og.Q_WBFS if args.workload == "rmat-wbfs" else og.Q_SSSP
+    kind = {"rmat-wbfs": og.Q_WBFS, "road-bf": og.Q_BF}.get(args.workload, og.Q_SSSP)
     cfg = None
     if not args.no_autotune and kind == og.Q_SSSP and not args.delta:
         lo, hi = (1 << 8, 1 << 16)
@@ -313,13 +315,29 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / kernel_s / 1e9
-    traffic = scaled_traffic("road" if args.workload == "road-sssp" else "rmat", g.n, nq,
-                             int(eff.engine))
+    traffic = scaled_traffic({"road-sssp": "road", "road-bf": "bf"}.get(args.workload, "rmat"),
+                             g.n, nq, int(eff.engine))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind, "kernel": "og_delta_kernel",
                 "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": round(kernel_s * 1e3, 3)}
+
+    ordered = None
+    if kind == og.Q_BF:
+        # the same sources by the ordered method (Delta-stepping with fusion), same GPU
+        ocfg = og.config(delta=4096, fusion_threshold=1024, expand_tile=32)
+        oq = [(og.Q_SSSP, int(s), 0, 0) for s in srcs]
+        og.batch_run(G, oq, cfg=ocfg, out=dbuf)
+        best = None
+        for _ in range(3):
+            _, _, ost = og.batch_run(G, oq, cfg=ocfg, out=dbuf)
+            if best is None or ost.kernel_ns < best.kernel_ns:
+                best = ost
+        ordered = {"schedule": "Delta 4096, fusion threshold 1024, tile 32",
+                   "kernel_ms": round(best.kernel_ns / 1e6, 3), "rounds": int(best.rounds),
+                   "relax": int(best.relax),
+                   "speedup_ordered": round(kernel_s * 1e9 / best.kernel_ns, 2)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -327,17 +345,19 @@ def run_ours(args):
 
     if rank == 0:
         value = m_r * world / step_s / 1e9
+        kname = {og.Q_SSSP: "SSSP", og.Q_WBFS: "wBFS", og.Q_BF: "Bellman-Ford"}[kind]
         line = {
-            "metric": "SSSP GTEPS (Delta-stepping with bucket fusion)" if kind == og.Q_SSSP
-            else "wBFS GTEPS",
+            "metric": {og.Q_SSSP: "SSSP GTEPS (Delta-stepping with bucket fusion)",
+                       og.Q_WBFS: "wBFS GTEPS",
+                       og.Q_BF: "SSSP GTEPS (unordered Bellman-Ford baseline)"}[kind],
             "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(step_s * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"{gname}: {nq} {'SSSP' if kind == og.Q_SSSP else 'wBFS'} "
-                                   f"sources per step, one persistent launch",
+            "config": {"workload": f"{gname}: {nq} {kname} sources per step, one persistent "
+                                   f"launch",
                        "n": g.n, "m": g.m, "sources_per_gpu": nq,
-                       "delta": 1 if kind == og.Q_WBFS else int(eff.delta),
+                       "delta": {og.Q_WBFS: 1, og.Q_BF: None}.get(kind, int(eff.delta)),
                        "fusion_threshold": int(eff.fusion_threshold),
                        "precheck": int(eff.precheck) == 1,
                        "expand_tile": int(eff.expand_tile),
@@ -354,6 +374,8 @@ def run_ours(args):
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "stats_per_step": {k: v // args.steps for k, v in agg.items()},
         }
+        if ordered is not None:
+            line["ordered"] = ordered
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

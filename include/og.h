@@ -51,6 +51,13 @@ extern "C" {
                             i * Delta >= best dist(src, dst) found so far             */
 #define OG_Q_ASTAR 2     /* dist(src, dst) with priority g + h, h = floor(100 * Euclid) */
 #define OG_Q_WBFS 3      /* SSSP with Delta = 1 (positive integer weights required)   */
+#define OG_Q_BF 4        /* all distances from src by unordered, frontier-based
+                            Bellman-Ford (the unordered baseline of Section 6's
+                            comparison): round r relaxes the out-edges of every vertex
+                            improved in round r - 1, with no priority order and no
+                            fusion.  Round engine only (a batch holding one runs on it);
+                            not accepted by the server or the autotuner.  The query's
+                            delta field is ignored.                                   */
 
 typedef struct og_graph og_graph;
 typedef struct og_server og_server;
@@ -176,6 +183,13 @@ int og_sssp_delta(og_graph* g, uint32_t src, uint32_t delta, uint32_t* dist_out,
 /* og_wbfs: weighted BFS = SSSP with Delta = 1 (Section 6.1, "SSSP and wBFS"); every
  * weight must be >= 1 (OG_E_INVALID otherwise). */
 int og_wbfs(og_graph* g, uint32_t src, uint32_t* dist_out, void* stream);
+
+/* og_sssp_bellman_ford: the same distances as og_sssp_delta, computed by the unordered
+ * Bellman-Ford baseline (OG_Q_BF); stats (may be NULL) receives its round count and
+ * work counters for the ordered-vs-unordered comparison (Section 6, "unordered
+ * GraphIt" rows). */
+int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats* stats,
+                         void* stream);
 
 /* og_ppsp: point-to-point distance (Section 6.1, "PPSP"): Delta-stepping from src that
  * stops on entering bucket i with i * Delta >= the best dist(src, dst) found.

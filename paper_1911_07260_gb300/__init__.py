@@ -21,7 +21,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "og.h")
 _lib = None
 
 OK, E_INVALID, E_OOM, E_CUDA, E_OVERFLOW, E_TIMEOUT, E_BUSY, E_ARENA, E_INTERNAL = range(9)
-Q_SSSP, Q_PPSP, Q_ASTAR, Q_WBFS = 0, 1, 2, 3
+Q_SSSP, Q_PPSP, Q_ASTAR, Q_WBFS, Q_BF = 0, 1, 2, 3, 4
 FUSION_OFF = 0xFFFFFFFE
 FUSION_UNBOUNDED = 0xFFFFFFFF
 ENGINE_DEFAULT, ENGINE_ROUNDS, ENGINE_ASYNC = 0, 1, 2
@@ -87,6 +87,7 @@ def lib():
             "og_graph_free": (None, [vp]),
             "og_config_default": (None, [P(Config)]),
             "og_sssp_delta": (i32, [vp, u32, u32, vp, vp]),
+            "og_sssp_bellman_ford": (i32, [vp, u32, vp, P(Stats), vp]),
             "og_wbfs": (i32, [vp, u32, vp, vp]),
             "og_ppsp": (i32, [vp, u32, u32, u32, P(u32), vp]),
             "og_astar": (i32, [vp, u32, u32, vp, u32, P(u32), vp]),
@@ -244,6 +245,15 @@ def sssp_delta(g: Graph, src: int, delta: int = 0, out=None, stream=None):
     return out
 
 
+def bellman_ford(g: Graph, src: int, out=None, stream=None):
+    """Unordered frontier-based Bellman-Ford; returns (``out`` uint32[n], Stats)."""
+    out = _alloc_dist(g, out)
+    st = Stats()
+    _check(lib().og_sssp_bellman_ford(g.handle, src, _ptr(out), ctypes.byref(st), _stream(stream)),
+           "og_sssp_bellman_ford")
+    return out, st
+
+
 def wbfs(g: Graph, src: int, out=None, stream=None):
     """Weighted BFS (Delta = 1); returns ``out`` (uint32[n])."""
     out = _alloc_dist(g, out)
@@ -272,7 +282,7 @@ def query_run(g: Graph, kind: int, src: int, dst: int = 0, delta: int = 0, cfg=N
     q = Query(kind, src, dst, delta)
     st = Stats()
     d = ctypes.c_uint32()
-    if out is None and kind in (Q_SSSP, Q_WBFS):
+    if out is None and kind in (Q_SSSP, Q_WBFS, Q_BF):
         out = np.empty(g.n, np.uint32)
     _check(lib().og_query_run(g.handle, ctypes.byref(q), ctypes.byref(cfg) if cfg else None,
                               _ptr(out), ctypes.byref(d), ctypes.byref(st), _stream(stream)),

@@ -307,7 +307,7 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
   uint32_t min_delta = 0xFFFFFFFFu;
   bool astar = false;
   for (uint32_t i = 0; i < nq; ++i) {
-    min_delta = std::min(min_delta, qd[i].delta);
+    if (qd[i].kind != kBF) min_delta = std::min(min_delta, qd[i].delta);  // BF: 2 buckets
     astar |= qd[i].kind == kASTAR;
   }
   const uint32_t B = ring_size(g, c, min_delta);
@@ -418,7 +418,8 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     for (uint32_t i = 0; i < nq; ++i)
       if (hq[i].aborted) pending.push_back(i);
     for (uint32_t i = 0; i < nq; ++i)
-      if (!hq[i].aborted && d_out) d_out[i] = qd[i].kind == kSSSP ? 0u : hq[i].result;
+      if (!hq[i].aborted && d_out)
+        d_out[i] = (qd[i].kind == kPPSP || qd[i].kind == kASTAR) ? hq[i].result : 0u;
     if (pending.empty()) break;
     // Some queries ran out of bucket space: rerun just those with twice the arena.
     if (attempt >= 6) return OG_E_ARENA;
@@ -606,7 +607,9 @@ int run_chunk_async(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq,
 
 int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
               uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
-  if (c.engine == OG_ENGINE_ASYNC)
+  bool bf = false;
+  for (uint32_t i = 0; i < nq; ++i) bf |= qd[i].kind == kBF;
+  if (c.engine == OG_ENGINE_ASYNC && !bf)  // Bellman-Ford rounds need the round engine
     return run_chunk_async(g, ws, qd, nq, c, dist_dev, d_out, acc, ro, st);
   return run_chunk_rounds(g, ws, qd, nq, c, dist_dev, d_out, acc, ro, st);
 }
@@ -660,6 +663,10 @@ int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d
       }
       d->delta = q.delta ? q.delta : c.delta;
       break;
+    case OG_Q_BF:
+      d->kind = kBF;
+      d->delta = 0;  // no buckets by distance: one bucket per round
+      return OG_OK;
     default:
       return OG_E_INVALID;
   }
@@ -892,6 +899,13 @@ int og_wbfs(og_graph* g, uint32_t src, uint32_t* dist_out, void* stream) {
   return og_query_run(g, &q, nullptr, dist_out, nullptr, nullptr, stream);
 }
 
+int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats* stats,
+                         void* stream) {
+  if (!dist_out) return OG_E_INVALID;
+  og_query q{OG_Q_BF, src, 0, 0};
+  return og_query_run(g, &q, nullptr, dist_out, nullptr, stats, stream);
+}
+
 int og_ppsp(og_graph* g, uint32_t src, uint32_t dst, uint32_t delta, uint32_t* d_out,
             void* stream) {
   if (!d_out) return OG_E_INVALID;
@@ -986,6 +1000,7 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
 int og_server_submit(og_server* s, const og_query* q, uint64_t tag) {
   if (!s || !q) return OG_E_INVALID;
   if (s->free_list.empty()) return OG_E_BUSY;
+  if (q->kind == OG_Q_BF) return OG_E_INVALID;  // the server runs the barrier-free engine
   QDesc d;
   TRY(make_desc(s->g, *q, s->cfg, &d));
   const uint32_t slot = s->free_list.back();

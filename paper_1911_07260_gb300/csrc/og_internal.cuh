@@ -24,7 +24,9 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kMaxQ = 512;               // queries per launch
 constexpr int kMaxRing = 256;            // materialised buckets per query
 
-enum Kind : uint32_t { kSSSP = 0, kPPSP = 1, kASTAR = 2 };
+// kBF: unordered Bellman-Ford; its QDesc.delta is 0 and every insert goes to bucket
+// cur + 1, so a bucket is one round's frontier.
+enum Kind : uint32_t { kSSSP = 0, kPPSP = 1, kASTAR = 2, kBF = 3 };
 
 enum Phase : uint32_t {
   kPhRelax = 0,      // process the current buckets (frontier pass + fused local loop)

@@ -162,7 +162,9 @@ __device__ __forceinline__ void relax_edges(const Params& P, Smem& S, const Bins
     C.relax += ok[k] ? 1u : 0u;
     C.improved += ins ? 1u : 0u;
     if (ins && P.prefetch) prefetch_row(P.ell, P.off, ew[k].x);
-    const uint32_t key = ins ? bucket_of(nd[k], h[k], S.delta[q[k]]) : 0u;
+    // Delta 0 marks a Bellman-Ford query: the next round's bucket, whatever the distance.
+    const uint32_t dq = S.delta[q[k]];
+    const uint32_t key = ins ? (dq ? bucket_of(nd[k], h[k], dq) : S.cur[q[k]] + 1u) : 0u;
     insert_warp(P, S, B, out, ins, allow_local, ew[k].x, nd[k], key, q[k], C);
   }
 }
@@ -502,7 +504,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
       const QDesc* qd = P.qd + q;
       const uint32_t kind = __ldg(&qd->kind);
       const uint32_t dst = __ldg(&qd->dst);
-      if (active && !redist && kind != kSSSP && !__ldcg(&qs->no_exit)) {
+      if (active && !redist && (kind == kPPSP || kind == kASTAR) && !__ldcg(&qs->no_exit)) {
         // Stop rule of Section 6.1 (PPSP): entering bucket i with i * Delta >= the best
         // distance to the target found so far.
         const uint32_t dt = __ldcg(P.dist + (size_t)q * P.n + dst);
@@ -702,7 +704,7 @@ __device__ void redist_min_phase(const Params& P) {
       const uint2 en = __ldcg(pile + i);
       if (__ldcg(P.dist + (size_t)q * P.n + en.x) != en.y) continue;
       const uint32_t h = astar ? heuristic(P.xy, P.xy_integral, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
-      best = min(best, bucket_of(en.y, h, delta));
+      best = min(best, delta ? bucket_of(en.y, h, delta) : __ldcg(&qs->redist_min));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULL, best, o));
@@ -729,7 +731,7 @@ __device__ void redist_move_phase(const Params& P) {
       const uint2 en = __ldcg(pile + i);
       if (__ldcg(P.dist + (size_t)q * P.n + en.x) != en.y) continue;
       const uint32_t h = astar ? heuristic(P.xy, P.xy_integral, en.x, __ldg(&qd->tx), __ldg(&qd->ty)) : 0u;
-      const uint32_t key = bucket_of(en.y, h, delta);
+      const uint32_t key = delta ? bucket_of(en.y, h, delta) : cur;
       bool to_pile = true;
       if (key - cur < P.B) {
         const uint32_t cid = q * P.B + (key & P.Bmask);
@@ -868,7 +870,7 @@ extern "C" __global__ void og_init_kernel(Params P, const uint32_t* slots, uint3
   const QDesc d = P.qd[q];
   P.dist[(size_t)q * P.n + d.src] = 0u;
   const uint32_t h0 = d.kind == kASTAR ? heuristic(P.xy, P.xy_integral, d.src, d.tx, d.ty) : 0u;
-  const uint32_t key0 = bucket_of(0u, h0, d.delta);
+  const uint32_t key0 = d.delta ? bucket_of(0u, h0, d.delta) : 0u;
   uint32_t* cnts = P.counts + (size_t)q * P.B;
   for (uint32_t k = 0; k < P.B; ++k) cnts[k] = 0u;
   cnts[key0 & P.Bmask] = 1u;

@@ -430,3 +430,62 @@ def test_autotune_batch_mixed_queries(og, orc, gg, road300):
             og.autotune_batch(G, bad)
         assert e.value.code == og.E_INVALID
     G.set_config(og.Config())  # the fixture's graph goes back to library defaults
+
+
+def test_bellman_ford_matches_oracle(og, orc, gg, grid256, road300):
+    """The unordered Bellman-Ford baseline (OG_Q_BF) reaches the oracle's distances on the
+    grid, the road-like graph, R-MAT with weights up to 2^16 and ragged random graphs
+    with zero weights, self loops and unreachable parts."""
+    cases = [(grid256[0], grid256[1], [0, 4321]), (road300[0], road300[1], None)]
+    r = gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1 << 16, seed=4)
+    cases.append((r, og.Graph.from_csr(r), None))
+    for seed in (3, 8):
+        rg = gg.random_graph(1500, 6000, 0, 20, seed=seed)
+        cases.append((rg, og.Graph.from_csr(rg), [0, 7]))
+    for g, G, srcs in cases:
+        srcs = srcs or [int(x) for x in gg.sample_sources(g, 2, seed=5)]
+        for s in srcs:
+            got, st = og.bellman_ford(G, s)
+            ref = orc.dijkstra(g, s)
+            np.testing.assert_array_equal(got, ref)
+            np.testing.assert_array_equal(got, orc.bellman_ford(g, s))
+            assert st.fused_iters == 0 and st.local_inserts == 0  # no fusion, no order
+
+
+def test_bellman_ford_round_count_is_hop_depth(og, gg):
+    """On a path of k edges round r settles vertex r, so Bellman-Ford needs at least k
+    rounds (and one more to see the frontier empty), while Delta-stepping with one wide
+    bucket and fusion settles the path in far fewer global rounds."""
+    k = 500
+    g = gg.path_graph([3] * k)
+    G = og.Graph.from_csr(g)
+    got, st = og.bellman_ford(G, 0)
+    np.testing.assert_array_equal(got, np.arange(k + 1, dtype=np.uint32) * 3)
+    assert k <= st.rounds <= k + 2
+    cfg = og.config(delta=1 << 20, fusion_threshold=og.FUSION_UNBOUNDED, engine=og.ENGINE_ROUNDS)
+    _, _, st2 = og.query_run(G, og.Q_SSSP, 0, cfg=cfg)
+    assert st2.rounds < st.rounds // 10
+
+
+def test_bellman_ford_in_batches_and_small_arenas(og, orc, gg, road300):
+    """A batch mixing Bellman-Ford with ordered queries runs on the round engine even
+    when the asynchronous engine is asked for; a two-bucket ring with a tiny arena forces
+    the overflow pile and its redistribution; the server rejects the kind."""
+    g, G = road300
+    s = [int(x) for x in gg.sample_sources(g, 4, seed=9)]
+    qs = [(og.Q_BF, s[0], 0, 0), (og.Q_SSSP, s[1], 0, 2048), (og.Q_PPSP, s[2], s[3], 2048),
+          (og.Q_BF, s[3], 0, 0)]
+    out, d, _ = og.batch_run(G, qs, cfg=og.config(engine=og.ENGINE_ASYNC))
+    out = out.reshape(4, g.n)
+    for i in (0, 1, 3):
+        np.testing.assert_array_equal(out[i], orc.dijkstra(g, qs[i][1]))
+    assert d[2] == orc.ppsp(g, s[2], s[3]) and d[0] == 0 and d[3] == 0
+    cfg = og.config(ring_buckets=2, arena_entries=2000)
+    got, _, st = og.query_run(G, og.Q_BF, s[0], cfg=cfg)
+    np.testing.assert_array_equal(got, orc.dijkstra(g, s[0]))
+    assert st.overflow_inserts > 0 or st.restarts > 0
+    srv = og.Server(G, max_slots=4)
+    with pytest.raises(og.OgError) as e:
+        srv.submit(og.Q_BF, s[0], 0, tag=1)
+    assert e.value.code == og.E_INVALID
+    srv.free()
