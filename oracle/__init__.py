@@ -2,7 +2,8 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this package.  It computes the plain definition of shortest-path distances
-(``oracle.c``: Dijkstra, BFS, Bellman-Ford, certificate check) and shares no code with
+(``oracle.c``: Dijkstra, BFS, Bellman-Ford, certificate check) and
+k-core coreness by peeling and shares no code with
 the CUDA path in ``paper_1911_07260_gb300``.
 
 Each wrapper takes a ``graphgen.Graph`` (CSR: uint64 offsets, uint32 neighbours,
@@ -53,6 +54,8 @@ def _load():
         L.or_bellman_ford.argtypes = [u32, vp, vp, vp, u32, vp]
         L.or_check_sssp.restype = ctypes.c_int
         L.or_check_sssp.argtypes = [u32, vp, vp, vp, u32, vp, vp]
+        L.or_kcore.restype = ctypes.c_int
+        L.or_kcore.argtypes = [u32, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -119,3 +122,11 @@ def check_sssp(g, src: int, dist: np.ndarray) -> tuple[int, int]:
     if code == INVALID:
         raise OracleError("invalid arguments")
     return int(code), int(bad.value)
+
+
+def kcore(g) -> np.ndarray:
+    """Coreness of every vertex (peeling; degrees count CSR entries)."""
+    off, nbr, _ = _csr(g)
+    out = np.empty(g.n, np.uint32)
+    _status(_load().or_kcore(g.n, off.ctypes.data, nbr.ctypes.data, out.ctypes.data), False)
+    return out

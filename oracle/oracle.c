@@ -21,6 +21,16 @@
  *                       reached, dist[v] <= dist[u] + w; every reached v != src has an
  *                       in-edge with equality; unreached vertices hold the sentinel.
  *                       With every weight >= 1 these conditions imply exactness.
+ *   - or_kcore:         coreness of every vertex by the peeling procedure the paper
+ *                       uses for k-core (Section 6.1, "k-core"): repeatedly take an
+ *                       unextracted vertex of minimum priority (priority = degree at
+ *                       the start), raise the level k to that priority if it is larger,
+ *                       record coreness = k, and lower by one the priority of every
+ *                       unextracted neighbour whose priority is above k (the constant
+ *                       -1 sum update, floored at k).  Degrees and decrements count CSR
+ *                       entries, so on a symmetric simple graph this is the usual
+ *                       coreness; the minimum is taken with the binary heap above
+ *                       (stale heap entries are skipped).
  *
  * Conventions.  Distances are uint32 with 0xFFFFFFFF = unreachable (the paper's INT_MAX
  * initialisation, Section 4.1).  A finite distance >= 0xFFFFFFFE cannot be represented;
@@ -196,4 +206,45 @@ int or_check_sssp(uint32_t n, const uint64_t *off, const uint32_t *nbr, const ui
     if (v != src && dist[v] != UNREACHED && !tight[v]) { *bad = v; code = 3; }
   free(tight);
   return code;
+}
+
+/* Coreness by peeling (see the header).  core_out: uint32[n]. */
+int or_kcore(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t *core_out) {
+  if (n == 0) return OR_INVALID;
+  const uint64_t m = off[n];
+  uint32_t *prio = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  unsigned char *done = (unsigned char *)calloc(n, 1);
+  heap_item *h = (heap_item *)malloc(sizeof(heap_item) * (n + m + 1));
+  if (!prio || !done || !h) {
+    free(prio);
+    free(done);
+    free(h);
+    return OR_NOMEM;
+  }
+  uint64_t hs = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    prio[v] = (uint32_t)(off[v + 1] - off[v]);
+    heap_item x = {prio[v], v};
+    heap_push(h, &hs, x);
+  }
+  uint32_t k = 0;
+  while (hs > 0) {
+    heap_item t = heap_pop(h, &hs);
+    uint32_t v = t.v;
+    if (done[v] || t.key != prio[v]) continue; /* extracted, or an older priority */
+    if (prio[v] > k) k = prio[v];
+    done[v] = 1;
+    core_out[v] = k;
+    for (uint64_t e = off[v]; e < off[v + 1]; ++e) {
+      uint32_t w = nbr[e];
+      if (done[w] || prio[w] <= k) continue;
+      prio[w] -= 1;
+      heap_item x = {prio[w], w};
+      heap_push(h, &hs, x);
+    }
+  }
+  free(prio);
+  free(done);
+  free(h);
+  return OR_OK;
 }

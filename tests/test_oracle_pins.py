@@ -194,3 +194,91 @@ def test_oracle_rejects_bad_arguments(gg, orc):
         orc.dijkstra(g, 3)
     with pytest.raises(orc.OracleError):
         orc.dijkstra(g, 0, target=9)
+
+
+# ---- k-core (coreness by peeling) -------------------------------------------------------
+
+def _sym(gg, n, pairs):
+    """Symmetric simple graph from undirected pairs (unit weights)."""
+    s = [u for u, v in pairs] + [v for u, v in pairs]
+    d = [v for u, v in pairs] + [u for u, v in pairs]
+    return gg.from_edges(n, s, d, [1] * len(s))
+
+
+def _core_brute(n, pairs):
+    """Coreness by its definition: the largest k such that v lies in a vertex set whose
+    induced subgraph has minimum degree >= k (every subset enumerated; tiny n only)."""
+    adj = [set() for _ in range(n)]
+    for u, v in pairs:
+        adj[u].add(v)
+        adj[v].add(u)
+    core = [0] * n
+    for r in range(1, n + 1):
+        for S in itertools.combinations(range(n), r):
+            Sset = set(S)
+            k = min(len(adj[v] & Sset) for v in S)
+            for v in S:
+                core[v] = max(core[v], k)
+    return core
+
+
+def test_kcore_closed_forms(gg, orc):
+    """Clique K_n: n - 1; cycle: 2; path and star: 1; isolated: 0; complete bipartite
+    K_{a,b}: min(a, b); 4-neighbour grid: 2 everywhere."""
+    n = 9
+    g = _sym(gg, n, list(itertools.combinations(range(n), 2)))
+    assert orc.kcore(g).tolist() == [n - 1] * n
+    g = _sym(gg, 12, [(i, (i + 1) % 12) for i in range(12)])
+    assert orc.kcore(g).tolist() == [2] * 12
+    g = _sym(gg, 8, [(i, i + 1) for i in range(6)])  # path on 0..6, vertex 7 isolated
+    assert orc.kcore(g).tolist() == [1] * 7 + [0]
+    g = _sym(gg, 10, [(0, i) for i in range(1, 10)])
+    assert orc.kcore(g).tolist() == [1] * 10
+    a, b = 4, 7
+    g = _sym(gg, a + b, [(i, a + j) for i in range(a) for j in range(b)])
+    assert orc.kcore(g).tolist() == [min(a, b)] * (a + b)
+    assert set(orc.kcore(gg.grid(17, 23, 1, 9, seed=3)).tolist()) == {2}
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_kcore_vs_definition_brute_force(gg, orc, seed):
+    """Random simple graphs on 9 vertices, densities from sparse to near-complete."""
+    rng = np.random.default_rng(seed)
+    n = 9
+    p = 0.15 + 0.07 * seed
+    pairs = [(u, v) for u, v in itertools.combinations(range(n), 2) if rng.random() < p]
+    g = _sym(gg, n, pairs)
+    assert orc.kcore(g).tolist() == _core_brute(n, pairs)
+
+
+def test_kcore_multigraph_counts_csr_entries():
+    """Hand-worked: with parallel edges every CSR entry counts toward the degree and
+    every removal lowers the neighbour once per entry.  Vertices 0 and 1 joined by three
+    parallel edges (both directions) and vertex 2 hanging off 1 by one edge:
+    deg = (3, 4, 1); 2 goes at level 1, then 1 drops to 3, and 0 and 1 stay 3-cores."""
+    import graphgen as gg
+    import oracle as orc
+    s = [0, 0, 0, 1, 1, 1, 1, 2]
+    d = [1, 1, 1, 0, 0, 0, 2, 1]
+    g = gg.from_edges(3, s, d, [1] * len(s))
+    assert orc.kcore(g).tolist() == [3, 3, 1]
+
+
+def test_kcore_level_sets_are_cores(gg, orc):
+    """On an R-MAT graph: for every k the vertices of coreness >= k induce a subgraph of
+    minimum degree >= k, and no vertex of coreness k has k + 1 neighbours of coreness
+    >= k + 1 (else adding it to them would give a larger (k+1)-core)."""
+    g = gg.rmat(11, 16, 0.57, 0.19, 0.19, 1, 2, seed=2)
+    core = orc.kcore(g).astype(np.int64)
+    off = g.offsets.astype(np.int64)
+    src = np.repeat(np.arange(g.n), np.diff(off))
+    dst = g.nbr.astype(np.int64)
+    for k in range(1, int(core.max()) + 1):
+        keep = core >= k
+        inside = keep[src] & keep[dst]
+        deg_in = np.bincount(src[inside], minlength=g.n)
+        assert (deg_in[keep] >= k).all()
+        up = core[dst] >= k + 1
+        at_k = core[src] == k
+        cnt = np.bincount(src[at_k & up], minlength=g.n)
+        assert (cnt[core == k] <= k).all()
