@@ -18,7 +18,8 @@ flush is needed between steps.
 Other workloads (--workload): rmat-wbfs, rmat-sssp (R-MAT scale 24), batch (256 queries
 on a 1024 x 1024 road-like grid, queries/s), serve (Poisson A*/PPSP stream, p50/p99),
 road-bf (the default graph and sources by the unordered Bellman-Ford baseline, with the
-ordered method's time on the same sources for the comparison of Section 6).
+ordered method's time on the same sources for the comparison of Section 6), rmat-kcore
+(coreness of R-MAT scale 24 by peeling, lazy with the histogram reduction and eager).
 
 --impl reference times the CPU oracle (single-threaded Dijkstra) on the same workload
 and metric, one bounded sample per step.
@@ -52,7 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="road-sssp",
-                   choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf"])
+                   choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf",
+                            "rmat-kcore"])
     p.add_argument("--side", type=int, default=4900, help="road-like grid side")
     p.add_argument("--scale", type=int, default=24, help="R-MAT scale")
     p.add_argument("--sources", type=int, default=8)
@@ -641,6 +643,99 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kcore(args):
+    """k-core of the R-MAT scale-24 graph (Section 6.1): one peeling per step, lazy bucket
+    update with the histogram reduction; the eager update timed beside it (Section 6.4's
+    eager-vs-lazy table).  GTEPS = directed edges / device time per step."""
+    import torch
+    import graphgen
+    import oracle
+    import paper_1911_07260_gb300 as og
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    g = graphgen.rmat(args.scale, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
+    G = og.Graph.from_csr(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    core, st0 = og.kcore(G, og.KCORE_LAZY, out=out)
+    ref_core = out.cpu().numpy().view(np.uint32).copy()
+    for _ in range(args.warmup):
+        og.kcore(G, og.KCORE_LAZY, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernel_ns = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, st = og.kcore(G, og.KCORE_LAZY, out=out)
+            kernel_ns += st.kernel_ns
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    kernel_s = kernel_ns / 1e9 / args.steps
+    clocks = clk.summary()
+    same = True
+    best_e = None
+    for _ in range(max(2, args.steps // 5)):
+        _, se = og.kcore(G, og.KCORE_EAGER, out=out)
+        same &= bool(np.array_equal(out.cpu().numpy().view(np.uint32), ref_core))
+        if best_e is None or se.kernel_ns < best_e.kernel_ns:
+            best_e = se
+    host = np.empty(g.n, np.uint32)
+    t0 = time.perf_counter()
+    reps = max(2, args.steps // 4)
+    for _ in range(reps):
+        og.kcore(G, og.KCORE_LAZY, out=host)
+    e2e_s = (time.perf_counter() - t0) / reps
+    same &= bool(np.array_equal(host, ref_core))
+    # bytes: per edge the neighbour id, its priority and its counter (4 + 4 + 4); per
+    # vertex offsets 8, priority init and final 8, one bucket insert and pop 8
+    bytes_step = 12 * g.m + 24 * g.n
+    peak, peak_kind = peaks()
+    cpu = None
+    if not args.no_cpu_baseline:
+        small = graphgen.rmat(20, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
+        t0 = time.perf_counter()
+        oracle.kcore(small)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(small.m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1,
+               "kind": "oracle",
+               "sample": f"the oracle's peeling (binary heap) on R-MAT scale 20 from the same "
+                         f"generator ({small.n} V, {small.m} E), {dt:.1f} s"}
+    line = {
+        "metric": "k-core GTEPS (directed edges / time, lazy bucket update with histogram)",
+        "value": round(g.m / step_s / 1e9, 4), "unit": "GTEPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"R-MAT scale {args.scale} k-core (coreness of every vertex), "
+                               "one persistent launch per step", "n": g.n, "m": g.m,
+                   "max_coreness": int(ref_core.max()),
+                   "l2": "inputs larger than L2 (graph %.0f MB)" % (8 * g.m / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round(bytes_step / kernel_s / 1e9 / peak, 4), "traffic": None,
+                     "peak_source": peak_kind, "kernel": "og_kcore_kernel",
+                     "bytes_per_launch": bytes_step, "kernel_ms": round(kernel_s * 1e3, 3)},
+        "eager": {"kernel_ms": round(best_e.kernel_ns / 1e6, 3), "rounds": int(best_e.rounds),
+                  "priority_updates": int(best_e.improved),
+                  "bucket_inserts": int(best_e.global_inserts),
+                  "lazy_speedup": round(best_e.kernel_ns / 1e9 / kernel_s, 2)},
+        "lazy": {"rounds": int(st.rounds), "levels": int(st.fused_iters),
+                 "priority_updates": int(st.improved), "bucket_inserts": int(st.global_inserts),
+                 "window_refills": int(st.redistributions), "scanned_levels": int(st.flushes)},
+        "exact_lazy_eq_eager_eq_host": same,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(g.m / e2e_s / 1e9, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * g.n, "ms_per_step": round(e2e_s * 1e3, 3)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -648,6 +743,8 @@ def main(argv=None):
         return
     if args.workload == "batch":
         run_batch(args)
+    elif args.workload == "rmat-kcore":
+        run_kcore(args)
     elif args.workload == "serve":
         run_serve(args)
     else:

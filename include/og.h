@@ -191,6 +191,32 @@ int og_wbfs(og_graph* g, uint32_t src, uint32_t* dist_out, void* stream);
 int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats* stats,
                          void* stream);
 
+/* og_kcore: coreness of every vertex (Section 6.1, "k-core"): the largest k such that the
+ * vertex belongs to a subgraph whose vertices all have degree >= k, computed by peeling
+ * with buckets of vertex priorities (priority = degree at the start; the minimum
+ * non-empty bucket is the level k; extracting a vertex lowers every neighbour whose
+ * priority is above k by one, floored at k).  The graph must be symmetric (each
+ * undirected edge stored in both directions); degrees and decrements count CSR entries,
+ * so on a simple symmetric graph this is the usual coreness.  Weights are ignored.
+ *   mode: OG_KCORE_LAZY -- lazy bucket update with the constant-sum (histogram)
+ *         reduction of Section 5.1: one priority update and one bucket insertion per
+ *         vertex and round; OG_KCORE_EAGER -- eager update (Section 3.2): one
+ *         compare-and-swap decrement and one bucket insertion per edge.
+ *   cfg: NULL or a config; used fields: expand_tile (frontier entries per claim, rounded
+ *        up to 256), blocks_per_sm, spin_limit_ns, arena_entries (vertex ids held by the
+ *        256 materialised buckets; default 4n; a bucket that runs out of space is rebuilt
+ *        by a scan at its level, so any size gives the same result).
+ *   core_out: uint32[n], host or device.  stats (may be NULL): rounds = peeling rounds,
+ *        fused_iters = levels extracted, items / stale = frontier entries / entries
+ *        already extracted, relax = edges scanned, improved = priority updates,
+ *        global_inserts = bucket insertions, redistributions = window refills,
+ *        flushes = levels rebuilt by a scan, kernel_ns, t_barrier_ns.
+ * Returns OG_E_INVALID for a bad mode or NULL output. */
+#define OG_KCORE_LAZY 0u
+#define OG_KCORE_EAGER 1u
+int og_kcore(og_graph* g, uint32_t mode, const og_config* cfg, uint32_t* core_out,
+             og_stats* stats, void* stream);
+
 /* og_ppsp: point-to-point distance (Section 6.1, "PPSP"): Delta-stepping from src that
  * stops on entering bucket i with i * Delta >= the best dist(src, dst) found.
  * d_out: host uint32, receives dist(src, dst) (0xFFFFFFFF if unreachable). */

@@ -28,6 +28,7 @@ ENGINE_DEFAULT, ENGINE_ROUNDS, ENGINE_ASYNC = 0, 1, 2
 PRECHECK_ON, PRECHECK_OFF = 1, 2
 LAYOUT_CSR, LAYOUT_ELL = 1, 2
 PREFETCH_ON, PREFETCH_OFF = 1, 2
+KCORE_LAZY, KCORE_EAGER = 0, 1
 UNREACHED = 0xFFFFFFFF
 
 
@@ -88,6 +89,7 @@ def lib():
             "og_config_default": (None, [P(Config)]),
             "og_sssp_delta": (i32, [vp, u32, u32, vp, vp]),
             "og_sssp_bellman_ford": (i32, [vp, u32, vp, P(Stats), vp]),
+            "og_kcore": (i32, [vp, u32, P(Config), vp, P(Stats), vp]),
             "og_wbfs": (i32, [vp, u32, vp, vp]),
             "og_ppsp": (i32, [vp, u32, u32, u32, P(u32), vp]),
             "og_astar": (i32, [vp, u32, u32, vp, u32, P(u32), vp]),
@@ -251,6 +253,15 @@ def bellman_ford(g: Graph, src: int, out=None, stream=None):
     st = Stats()
     _check(lib().og_sssp_bellman_ford(g.handle, src, _ptr(out), ctypes.byref(st), _stream(stream)),
            "og_sssp_bellman_ford")
+    return out, st
+
+
+def kcore(g: Graph, mode: int = KCORE_LAZY, cfg=None, out=None, stream=None):
+    """Coreness of every vertex by peeling; returns (``out`` uint32[n], Stats)."""
+    out = _alloc_dist(g, out)
+    st = Stats()
+    _check(lib().og_kcore(g.handle, mode, ctypes.byref(cfg) if cfg else None, _ptr(out),
+                          ctypes.byref(st), _stream(stream)), "og_kcore")
     return out, st
 
 

@@ -33,6 +33,10 @@ cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t s
 cudaError_t async_occupancy(int* blocks_per_sm, size_t smem, bool ell);
 cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,
                               cudaStream_t st);
+cudaError_t kcore_occupancy(int* blocks_per_sm);
+cudaError_t launch_kcore(const KParams& P, int grid, cudaStream_t st);
+cudaError_t launch_kcore_init(const uint32_t* off, uint32_t* prio, uint32_t n, int sms,
+                              cudaStream_t st);
 }  // namespace og
 
 using namespace og;
@@ -107,7 +111,8 @@ struct HBuf {
 // Device scratch of one launch configuration (grown on demand, reused across calls).
 struct Workspace {
   DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big, bmap;
-  HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq;
+  DBuf kprio, kcnt, ktouched, klist, kring, kcounts, klossy, kstate;  // k-core
+  HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq, h_kstate;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // Barrier-free engine: ring positions must read "free" (all ones) before use.  Entries
   // [0, clean_upto) of the ring are known free except the listed dirty ranges.
@@ -116,9 +121,10 @@ struct Workspace {
   void* ring_ptr = nullptr;
   void release() {
     for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
-                    &big, &bmap})
+                    &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
+                    &kstate})
       b->release();
-    for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq}) b->release();
+    for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq, &h_kstate}) b->release();
     clean_upto = 0;
     dirty.clear();
     ring_ptr = nullptr;
@@ -904,6 +910,102 @@ int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats
   if (!dist_out) return OG_E_INVALID;
   og_query q{OG_Q_BF, src, 0, 0};
   return og_query_run(g, &q, nullptr, dist_out, nullptr, stats, stream);
+}
+
+int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_out,
+             og_stats* stats, void* stream) {
+  if (!g || !core_out || mode > OG_KCORE_EAGER) return OG_E_INVALID;
+  const og_config c = resolve(g, ucfg);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& ws = g->ws;
+  const uint32_t n = g->n;
+  if (!g->sms) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int occ = 0;
+  CK(kcore_occupancy(&occ));
+  if (occ < 1) return OG_E_CUDA;
+  const int bps = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
+  const bool dev_out = is_device_ptr(core_out);
+  uint32_t* prio = core_out;
+  if (!dev_out) {
+    TRY(ws.kprio.ensure(sizeof(uint32_t) * (size_t)n));
+    prio = ws.kprio.as<uint32_t>();
+  }
+  // Window buckets: arena_entries vertex ids in all (default 4n, at least 1024 a bucket).
+  const uint64_t entries = c.arena_entries ? c.arena_entries : 4ull * n;
+  const uint64_t cap64 = std::max<uint64_t>(1024, entries / kKRing);
+  if (cap64 >= 0xFFFFFFF0ull) return OG_E_INVALID;
+  TRY(ws.kcnt.ensure(sizeof(uint32_t) * (size_t)n));
+  TRY(ws.ktouched.ensure(sizeof(uint32_t) * (size_t)n));
+  TRY(ws.klist.ensure(2 * sizeof(uint32_t) * (size_t)n));
+  TRY(ws.kring.ensure(sizeof(uint32_t) * (size_t)kKRing * cap64));
+  TRY(ws.kcounts.ensure(sizeof(uint32_t) * kKRing));
+  TRY(ws.klossy.ensure(sizeof(uint32_t) * kKRing));
+  TRY(ws.kstate.ensure(sizeof(KState)));
+  TRY(ws.sync.ensure(sizeof(Sync)));
+  TRY(ws.stats.ensure(sizeof(Stats)));
+  TRY(ws.h_sync.ensure(sizeof(Sync)));
+  TRY(ws.h_stats.ensure(sizeof(Stats)));
+  TRY(ws.h_kstate.ensure(sizeof(KState)));
+  TRY(ws.events());
+  KParams P{};
+  P.off = g->off;
+  P.adj = g->adj;
+  P.n = n;
+  P.prio = prio;
+  P.cnt = ws.kcnt.as<uint32_t>();
+  P.touched = ws.ktouched.as<uint32_t>();
+  P.list[0] = ws.klist.as<uint32_t>();
+  P.list[1] = P.list[0] + n;
+  P.ring = ws.kring.as<uint32_t>();
+  P.counts = ws.kcounts.as<uint32_t>();
+  P.lossy = ws.klossy.as<uint32_t>();
+  P.sync = ws.sync.as<Sync>();
+  P.ks = ws.kstate.as<KState>();
+  P.stats = ws.stats.as<Stats>();
+  P.cap = (uint32_t)cap64;
+  P.eager = mode == OG_KCORE_EAGER ? 1u : 0u;
+  P.tile = std::max<uint32_t>(kBlock, (c.expand_tile + kBlock - 1) / kBlock * kBlock);
+  P.spin_ns = c.spin_limit_ns;
+  CK(cudaMemsetAsync(P.cnt, 0, sizeof(uint32_t) * (size_t)n, st));
+  CK(cudaMemsetAsync(P.counts, 0, sizeof(uint32_t) * kKRing, st));
+  CK(cudaMemsetAsync(P.lossy, 0, sizeof(uint32_t) * kKRing, st));
+  CK(cudaMemsetAsync(P.ks, 0, sizeof(KState), st));
+  CK(cudaMemsetAsync(P.sync, 0, sizeof(Sync), st));
+  CK(cudaMemsetAsync(P.stats, 0, sizeof(Stats), st));
+  CK(launch_kcore_init(g->off, prio, n, g->sms, st));
+  CK(cudaEventRecord(ws.e0, st));
+  CK(launch_kcore(P, g->sms * bps, st));
+  CK(cudaEventRecord(ws.e1, st));
+  CK(cudaMemcpyAsync(ws.h_sync.p, P.sync, sizeof(Sync), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ws.h_stats.p, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ws.h_kstate.p, P.ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  if (!dev_out)
+    CK(cudaMemcpyAsync(core_out, prio, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ws.e0, ws.e1));
+  const Sync* hy = ws.h_sync.as<Sync>();
+  const KState* hk = ws.h_kstate.as<KState>();
+  Stats acc = *ws.h_stats.as<Stats>();
+  acc.v[15] = (unsigned long long)(ms * 1.0e6);
+  acc.v[kStFused] = hk->levels;
+  acc.v[kStRedist] = hk->refills;
+  acc.v[kStFlush] = hk->scans;
+  export_stats(acc, 0, stats);
+  if (hy->err & kErrBounds) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
+             hy->bad_code, hy->bad_val, hy->bad_aux);
+    return OG_E_INTERNAL;
+  }
+  if (hy->err & kErrTimeout) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "grid barrier wait gave up");
+    return OG_E_TIMEOUT;
+  }
+  return OG_OK;
 }
 
 int og_ppsp(og_graph* g, uint32_t src, uint32_t dst, uint32_t delta, uint32_t* d_out,

@@ -489,3 +489,77 @@ def test_bellman_ford_in_batches_and_small_arenas(og, orc, gg, road300):
         srv.submit(og.Q_BF, s[0], 0, tag=1)
     assert e.value.code == og.E_INVALID
     srv.free()
+
+
+def _sym_pairs(gg, n, pairs):
+    pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
+    s = np.concatenate([pairs[:, 0], pairs[:, 1]])
+    d = np.concatenate([pairs[:, 1], pairs[:, 0]])
+    return gg.from_edges(n, s, d, np.ones(s.size, np.uint32))
+
+
+def _cliques(sizes, gap=3):
+    """Disjoint cliques (coreness size - 1) plus `gap` isolated vertices after each."""
+    pairs, base = [], 0
+    for k in sizes:
+        idx = np.arange(base, base + k)
+        a, b = np.triu_indices(k, 1)
+        pairs.append(np.stack([idx[a], idx[b]], 1))
+        base += k + gap
+    return base, np.concatenate(pairs)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_kcore_matches_oracle(og, orc, gg, grid256, road300, mode):
+    """Coreness, lazy (histogram) and eager, equals the oracle's peeling on the grid, the
+    road-like graph, R-MAT (skewed, isolated vertices), random simple graphs, cliques and
+    stars."""
+    graphs = [grid256[0], road300[0], gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 2, seed=6)]
+    rng = np.random.default_rng(4)
+    for n, m in ((500, 3000), (2000, 30000)):
+        p = rng.integers(0, n, (m, 2))
+        p = np.unique(np.sort(p[p[:, 0] != p[:, 1]], 1), axis=0)
+        graphs.append(_sym_pairs(gg, n, p))
+    n, p = _cliques([1, 2, 5, 40])
+    graphs.append(_sym_pairs(gg, n, p))
+    graphs.append(_sym_pairs(gg, 50, [(0, i) for i in range(1, 50)]))
+    for g in graphs:
+        got, st = og.kcore(og.Graph.from_csr(g), mode)
+        np.testing.assert_array_equal(got, orc.kcore(g))
+        assert st.fused_iters >= 1 and st.rounds >= st.fused_iters
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_kcore_overflowing_buckets_and_window_refills(og, orc, gg, mode):
+    """Buckets of 1024 ids overflow on R-MAT's low levels, whose frontiers are then
+    rebuilt by scans; cliques of 10, 300 and 600 vertices put coreness levels more than
+    256 apart, so the 256-bucket window is refilled twice.  Both stay exact; a device
+    output buffer gives the same values."""
+    r = gg.rmat(14, 16, 0.57, 0.19, 0.19, 1, 2, seed=7)
+    got, st = og.kcore(og.Graph.from_csr(r), mode, cfg=og.config(arena_entries=1))
+    np.testing.assert_array_equal(got, orc.kcore(r))
+    assert st.flushes > 0
+    n, p = _cliques([10, 300, 600])
+    g = _sym_pairs(gg, n, p)
+    G = og.Graph.from_csr(g)
+    got, st = og.kcore(G, mode)
+    ref = orc.kcore(g)
+    np.testing.assert_array_equal(got, ref)
+    assert sorted(set(ref.tolist())) == [0, 9, 299, 599] and st.redistributions >= 2
+    dev = _dev(g.n)
+    og.kcore(G, mode, out=dev)
+    np.testing.assert_array_equal(_np(dev), ref)
+
+
+def test_kcore_lazy_makes_fewer_updates_than_eager(og, orc, gg):
+    """The histogram reduction applies one update per vertex and round where the eager
+    update applies one per edge (Section 5.1); the results agree."""
+    r = gg.rmat(14, 16, 0.57, 0.19, 0.19, 1, 2, seed=8)
+    G = og.Graph.from_csr(r)
+    a, sa = og.kcore(G, og.KCORE_LAZY)
+    b, sb = og.kcore(G, og.KCORE_EAGER)
+    np.testing.assert_array_equal(a, b)
+    assert sa.improved < sb.improved and sa.global_inserts < sb.global_inserts
+    with pytest.raises(og.OgError) as e:
+        og.kcore(G, 7)
+    assert e.value.code == og.E_INVALID
