@@ -203,14 +203,18 @@ int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats
  *         vertex and round; OG_KCORE_EAGER -- eager update (Section 3.2): one
  *         compare-and-swap decrement and one bucket insertion per edge.
  *   cfg: NULL or a config; used fields: expand_tile (frontier entries per claim, rounded
- *        up to 256), blocks_per_sm, spin_limit_ns, arena_entries (vertex ids held by the
+ *        up to 256), hub_degree (frontier vertices of at least this out-degree have
+ *        their edges split over every warp of the grid), blocks_per_sm, spin_limit_ns,
+ *        arena_entries (vertex ids held by the
  *        256 materialised buckets; default 4n; a bucket that runs out of space is rebuilt
  *        by a scan at its level, so any size gives the same result).
  *   core_out: uint32[n], host or device.  stats (may be NULL): rounds = peeling rounds,
  *        fused_iters = levels extracted, items / stale = frontier entries / entries
  *        already extracted, relax = edges scanned, improved = priority updates,
  *        global_inserts = bucket insertions, redistributions = window refills,
- *        flushes = levels rebuilt by a scan, kernel_ns, t_barrier_ns.
+ *        flushes = levels rebuilt by a scan, kernel_ns, and summed over CTAs:
+ *        t_frontier_ns (peel phases), t_fused_ns (lazy apply phases), t_hub_ns (hub
+ *        phases), t_barrier_ns.
  * Returns OG_E_INVALID for a bad mode or NULL output. */
 #define OG_KCORE_LAZY 0u
 #define OG_KCORE_EAGER 1u

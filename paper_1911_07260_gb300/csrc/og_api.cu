@@ -966,6 +966,17 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   P.sync = ws.sync.as<Sync>();
   P.ks = ws.kstate.as<KState>();
   P.stats = ws.stats.as<Stats>();
+  // Hubs (out-degree >= hub_degree) are split over every warp after the round's peel.
+  const uint32_t hub_cap = g->max_deg >= c.hub_degree ? kHubSlots : 0u;
+  if (hub_cap) {
+    TRY(ws.big.ensure(sizeof(BigItem) * hub_cap));
+    TRY(ws.bmap.ensure(sizeof(uint32_t) * kHubChunks));
+  }
+  P.hub = hub_cap ? ws.big.as<BigItem>() : nullptr;
+  P.hub_map = hub_cap ? ws.bmap.as<uint32_t>() : nullptr;
+  P.hub_cap = hub_cap;
+  P.map_cap = hub_cap ? kHubChunks : 0u;
+  P.hub_min = c.hub_degree;
   P.cap = (uint32_t)cap64;
   P.eager = mode == OG_KCORE_EAGER ? 1u : 0u;
   P.tile = std::max<uint32_t>(kBlock, (c.expand_tile + kBlock - 1) / kBlock * kBlock);

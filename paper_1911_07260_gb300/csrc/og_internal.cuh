@@ -154,6 +154,7 @@ enum KPhase : uint32_t {
   kKApply = 4,  // lazy: one priority update and one bucket insert per counted vertex
   kKStop = 5,
   kKPrologue = 6,
+  kKHub = 7,    // edges of the round's hub vertices, split over every warp of the grid
 };
 struct KState {
   uint32_t k;          // current level (priority of the bucket being extracted)
@@ -170,7 +171,8 @@ struct KState {
   uint32_t scans;      // levels rebuilt by a scan
   uint32_t refills;    // window refills
   uint32_t asel;       // list receiving the vertices that drop to k this round
-  uint32_t pad[1];
+  uint32_t hub_claim;  // hub pieces claimed in the hub phase
+  unsigned long long hub_word;  // (hubs listed << 32) | chunks reserved, this round
 };
 struct KParams {
   const uint32_t* off;
@@ -186,6 +188,9 @@ struct KParams {
   Sync* sync;
   KState* ks;
   Stats* stats;
+  BigItem* hub;         // frontier vertices of out-degree >= hub_min this round
+  uint32_t* hub_map;    // chunk -> hub slot
+  uint32_t hub_cap, map_cap, hub_min;
   uint32_t cap;
   uint32_t eager;       // 1: eager bucket update (a CAS decrement and an insert per edge)
   uint32_t tile;

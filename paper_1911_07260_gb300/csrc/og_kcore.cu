@@ -29,7 +29,7 @@ struct KSmem {
   uint32_t lb_pos[kBlock + 1];  // edge prefix sums of a sub-tile's entries
   uint32_t lb_beg[kBlock];
   uint32_t wtmp[kWarps + 1];
-  unsigned long long t_bar;
+  unsigned long long t_bar, t_peel, t_apply, t_hub;  // per-CTA phase time (thread 0)
 };
 
 struct KCnt {
@@ -110,6 +110,106 @@ __device__ __forceinline__ void kscan(uint32_t* a, uint32_t* wtmp) {
   __syncthreads();
 }
 
+// Applies the removal of level-k vertices to a batch of their out-neighbours w (lanes
+// with ok).  Lazy: each neighbour with a priority above k gets one count (the first
+// count lists it as touched).  Eager: the neighbour's priority is lowered by one
+// (compare-and-swap, floored at k) and the vertex goes to its new bucket.  All 32 lanes
+// must call it.
+__device__ __forceinline__ void update_batch(const KParams& P, const KSmem& S, KCnt& C,
+                                             const bool (&ok)[kKBatch],
+                                             const uint32_t (&w)[kKBatch]) {
+  const uint32_t k = S.k;
+  uint32_t p[kKBatch];
+#pragma unroll
+  for (int b = 0; b < kKBatch; ++b) p[b] = ok[b] ? __ldcg(P.prio + w[b]) : 0u;
+  if (!P.eager) {
+    bool first[kKBatch];
+#pragma unroll
+    for (int b = 0; b < kKBatch; ++b) {
+      const bool hit = ok[b] && p[b] > k;
+      first[b] = hit && atomicAdd(P.cnt + w[b], 1u) == 0u;
+      C.relax += ok[b] ? 1u : 0u;
+    }
+#pragma unroll
+    for (int b = 0; b < kKBatch; ++b)
+      if (!warp_append(P.touched, &P.ks->touched_n, P.n, first[b], w[b]))
+        report_bad(P.sync, 33u, w[b], 0u);
+  } else {
+#pragma unroll
+    for (int b = 0; b < kKBatch; ++b) {
+      // Each failed compare-and-swap means another thread lowered the priority, so the
+      // loop runs at most p - k times.
+      uint32_t c = p[b], np = 0;
+      bool dec = false;
+      while (ok[b] && c > k) {
+        const uint32_t prev = atomicCAS(P.prio + w[b], c, c - 1u);
+        if (prev == c) {
+          dec = true;
+          np = c - 1u;
+          break;
+        }
+        c = prev;
+      }
+      C.relax += ok[b] ? 1u : 0u;
+      C.improved += dec ? 1u : 0u;
+      insert_prio(P, S, C, dec, w[b], np);
+    }
+  }
+}
+
+// Lists a frontier vertex of out-degree >= hub_min for the hub phase: one 64-bit
+// atomicAdd reserves its slot (high word) and its range of kBigChunk-edge chunks (low
+// word); the chunk map names the slot of each chunk.  False when the list or the map is
+// full (the caller then expands the vertex itself).
+__device__ __noinline__ bool push_khub(const KParams& P, uint32_t u, uint32_t beg, uint32_t end) {
+  const uint32_t nch = (end - beg + kBigChunk - 1) / kBigChunk;
+  const unsigned long long x = atomicAdd(&P.ks->hub_word, (1ull << 32) | nch);
+  const uint32_t slot = (uint32_t)(x >> 32), cbase = (uint32_t)x;
+  const bool fits = slot < P.hub_cap && cbase <= P.map_cap && nch <= P.map_cap - cbase;
+  if (fits) {
+    BigItem it;
+    it.u = u;
+    it.g = 0;
+    it.q = 0;
+    it.beg = beg;
+    it.end = end;
+    it.cbase = cbase;
+    P.hub[slot] = it;
+  }
+  const uint32_t lim = cbase < P.map_cap ? min(P.map_cap - cbase, nch) : 0u;
+  for (uint32_t c = 0; c < lim; ++c) P.hub_map[cbase + c] = fits ? slot : kNone;
+  return fits;
+}
+
+// The hub phase: the warps of all CTAs claim 128-edge pieces of the round's hubs (one
+// counter; piece c lies in chunk c / 8, whose hub the chunk map names).
+__device__ void hub_phase(const KParams& P, KSmem& S, KCnt& C) {
+  const uint32_t lane = threadIdx.x & 31;
+  constexpr uint32_t kPiece = 32 * kKBatch, kPieces = kBigChunk / kPiece;
+  const uint32_t* nb = reinterpret_cast<const uint32_t*>(P.adj);
+  const uint32_t nsub = min((uint32_t)__ldcg(&P.ks->hub_word), P.map_cap) * kPieces;
+  for (;;) {
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(&P.ks->hub_claim, 1u);
+    c = __shfl_sync(FULL, c, 0);
+    if (c >= nsub) break;
+    const uint32_t slot = __ldcg(P.hub_map + c / kPieces);
+    if (slot >= P.hub_cap) continue;  // chunk of a hub that did not fit (expanded in place)
+    const BigItem* it = P.hub + slot;
+    const uint32_t hb = __ldcg(&it->beg), he = __ldcg(&it->end), cb = __ldcg(&it->cbase);
+    const uint32_t e0 = hb + (c / kPieces - cb) * kBigChunk + (c % kPieces) * kPiece;
+    bool ok[kKBatch];
+    uint32_t w[kKBatch];
+#pragma unroll
+    for (int b = 0; b < kKBatch; ++b) {
+      const uint32_t e = e0 + 32u * b + lane;
+      ok[b] = e < he;
+      w[b] = ok[b] ? __ldg(nb + 2 * (size_t)e) : 0u;
+    }
+    update_batch(P, S, C, ok, w);
+  }
+}
+
 // Extracts the frontier of level k.  CTAs claim tiles of frontier entries; a tile's live
 // entries (priority still k) have their out-degrees scanned and all threads walk the
 // joined edge list, thread t of a batch taking edge e0 + t.  Lazy: each neighbour with a
@@ -136,8 +236,12 @@ __device__ void peel_phase(const KParams& P, KSmem& S, KCnt& C) {
           C.items++;
           beg = __ldg(P.off + u);
           const uint32_t end = __ldg(P.off + u + 1);
-          if (__ldcg(P.prio + u) == k) deg = end - beg;
-          else C.stale++;  // priority fell below the bucket's level earlier: extracted
+          if (__ldcg(P.prio + u) == k) {
+            deg = end - beg;
+            if (deg >= P.hub_min && P.hub && push_khub(P, u, beg, end)) deg = 0;
+          } else {
+            C.stale++;  // priority fell below the bucket's level earlier: extracted
+          }
         } else {
           report_bad(P.sync, 31u, u, i);
         }
@@ -149,7 +253,7 @@ __device__ void peel_phase(const KParams& P, KSmem& S, KCnt& C) {
       const uint32_t etot = S.lb_pos[kBlock];
       for (uint32_t e0 = 0; e0 < etot; e0 += kBlock * kKBatch) {
         bool ok[kKBatch];
-        uint32_t w[kKBatch], p[kKBatch];
+        uint32_t w[kKBatch];
 #pragma unroll
         for (int b = 0; b < kKBatch; ++b) {
           const uint32_t idx = e0 + (uint32_t)b * kBlock + tid;
@@ -163,41 +267,7 @@ __device__ void peel_phase(const KParams& P, KSmem& S, KCnt& C) {
           const uint32_t e = S.lb_beg[j] + (idx - S.lb_pos[j]);
           w[b] = ok[b] ? __ldg(nb + 2 * (size_t)e) : 0u;
         }
-#pragma unroll
-        for (int b = 0; b < kKBatch; ++b) p[b] = ok[b] ? __ldcg(P.prio + w[b]) : 0u;
-        if (!P.eager) {
-          bool first[kKBatch];
-#pragma unroll
-          for (int b = 0; b < kKBatch; ++b) {
-            const bool hit = ok[b] && p[b] > k;
-            first[b] = hit && atomicAdd(P.cnt + w[b], 1u) == 0u;
-            C.relax += ok[b] ? 1u : 0u;
-          }
-#pragma unroll
-          for (int b = 0; b < kKBatch; ++b)
-            if (!warp_append(P.touched, &P.ks->touched_n, P.n, first[b], w[b]))
-              report_bad(P.sync, 33u, w[b], 0u);
-        } else {
-#pragma unroll
-          for (int b = 0; b < kKBatch; ++b) {
-            // Each failed compare-and-swap means another thread lowered the priority,
-            // so the loop runs at most p - k times.
-            uint32_t c = p[b], np = 0;
-            bool dec = false;
-            while (ok[b] && c > k) {
-              const uint32_t prev = atomicCAS(P.prio + w[b], c, c - 1u);
-              if (prev == c) {
-                dec = true;
-                np = c - 1u;
-                break;
-              }
-              c = prev;
-            }
-            C.relax += ok[b] ? 1u : 0u;
-            C.improved += dec ? 1u : 0u;
-            insert_prio(P, S, C, dec, w[b], np);
-          }
-        }
+        update_batch(P, S, C, ok, w);
       }
       __syncthreads();
     }
@@ -358,6 +428,18 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
         next = kKPeel;
         break;
       case kKPeel:
+        if ((__ldcg(&ks->hub_word) >> 32) > 0u) {  // hubs listed: their edges first
+          next = kKHub;
+          break;
+        }
+        if (!P.eager && __ldcg(&ks->touched_n) > 0u) next = kKApply;
+        else next = after_round();
+        break;
+      case kKHub:
+        if (lane == 0) {
+          ks->hub_word = 0ull;
+          ks->hub_claim = 0u;
+        }
         if (!P.eager && __ldcg(&ks->touched_n) > 0u) next = kKApply;
         else next = after_round();
         break;
@@ -432,16 +514,24 @@ extern "C" __global__ void __launch_bounds__(kBlock, 4) og_kcore_kernel(KParams 
   __shared__ KSmem S;
   KCnt C = {0, 0, 0, 0, 0};
   uint32_t bar = 0;
-  if (threadIdx.x == 0) S.t_bar = 0ull;
+  if (threadIdx.x == 0) S.t_bar = S.t_peel = S.t_apply = S.t_hub = 0ull;
   kbarrier(P, S, bar, kKPrologue);
   for (;;) {
     const uint32_t phase = S.phase;
     if (phase == kKStop || (S.err & kErrFatal)) break;
+    const uint64_t t0 = threadIdx.x == 0 ? gtimer() : 0ull;
     if (phase == kKMin) min_phase(P);
     else if (phase == kKFill) fill_phase(P, S, C);
     else if (phase == kKScan) scan_phase(P, S);
     else if (phase == kKPeel) peel_phase(P, S, C);
     else if (phase == kKApply) apply_phase(P, S, C);
+    else if (phase == kKHub) hub_phase(P, S, C);
+    if (threadIdx.x == 0) {
+      const uint64_t dt = gtimer() - t0;
+      if (phase == kKPeel) S.t_peel += dt;
+      else if (phase == kKApply) S.t_apply += dt;
+      else if (phase == kKHub) S.t_hub += dt;
+    }
     kbarrier(P, S, bar, phase);
   }
   const uint32_t lane = threadIdx.x & 31;
@@ -452,7 +542,12 @@ extern "C" __global__ void __launch_bounds__(kBlock, 4) og_kcore_kernel(KParams 
     const uint32_t s = warp_sum(vals[i]);
     if (lane == 0 && s) atomicAdd(&P.stats->v[idx[i]], (unsigned long long)s);
   }
-  if (threadIdx.x == 0) atomicAdd(&P.stats->v[kStTBarrier], S.t_bar);
+  if (threadIdx.x == 0) {
+    atomicAdd(&P.stats->v[kStTBarrier], S.t_bar);
+    atomicAdd(&P.stats->v[kStTFrontier], S.t_peel);
+    atomicAdd(&P.stats->v[kStTFused], S.t_apply);
+    atomicAdd(&P.stats->v[kStTHub], S.t_hub);
+  }
 }
 
 // priority <- out-degree

@@ -563,3 +563,19 @@ def test_kcore_lazy_makes_fewer_updates_than_eager(og, orc, gg):
     with pytest.raises(og.OgError) as e:
         og.kcore(G, 7)
     assert e.value.code == og.E_INVALID
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("hub", [8, 100, 0xFFFFFFFF])
+def test_kcore_hub_pass(og, orc, gg, mode, hub):
+    """Frontier vertices of out-degree >= hub_degree have their edges split over all warps
+    after the peel; thresholds down to 8 (most R-MAT edges) and none give the oracle's
+    coreness, with the cliques' levels far apart too."""
+    r = gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 2, seed=9)
+    cfg = og.config(hub_degree=hub)
+    got, _ = og.kcore(og.Graph.from_csr(r), mode, cfg=cfg)
+    np.testing.assert_array_equal(got, orc.kcore(r))
+    n, p = _cliques([12, 280])
+    g = _sym_pairs(gg, n, p)
+    got, _ = og.kcore(og.Graph.from_csr(g), mode, cfg=cfg)
+    np.testing.assert_array_equal(got, orc.kcore(g))
