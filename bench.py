@@ -724,10 +724,11 @@ def run_kcore(args):
                   "bucket_inserts": int(best_e.global_inserts),
                   "lazy_speedup": round(best_e.kernel_ns / 1e9 / kernel_s, 2)},
         "lazy": {"rounds": int(st.rounds), "levels": int(st.fused_iters),
-                 "cta_ms": {"peel": round(st.t_frontier_ns / 1e6 / 456, 1),
-                            "apply": round(st.t_fused_ns / 1e6 / 456, 1),
-                            "hub": round(st.t_hub_ns / 1e6 / 456, 1),
-                            "barrier": round(st.t_barrier_ns / 1e6 / 456, 1)},
+                 "cta_time_share": {
+                     k: round(v / max(1, st.t_frontier_ns + st.t_fused_ns + st.t_hub_ns
+                                      + st.t_barrier_ns), 3)
+                     for k, v in (("peel", st.t_frontier_ns), ("apply", st.t_fused_ns),
+                                  ("hub", st.t_hub_ns), ("barrier", st.t_barrier_ns))},
                  "priority_updates": int(st.improved), "bucket_inserts": int(st.global_inserts),
                  "window_refills": int(st.redistributions), "scanned_levels": int(st.flushes)},
         "exact_lazy_eq_eager_eq_host": same,
