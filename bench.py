@@ -19,7 +19,9 @@ Other workloads (--workload): rmat-wbfs, rmat-sssp (R-MAT scale 24), batch (256 
 on a 1024 x 1024 road-like grid, queries/s), serve (Poisson A*/PPSP stream, p50/p99),
 road-bf (the default graph and sources by the unordered Bellman-Ford baseline, with the
 ordered method's time on the same sources for the comparison of Section 6), rmat-kcore
-(coreness of R-MAT scale 24 by peeling, lazy with the histogram reduction and eager).
+(coreness of R-MAT scale 24 by peeling, lazy with the histogram reduction and eager),
+road-lazy / rmat-lazy (SSSP with the lazy bucket update, the eager update's time on the
+same sources beside it: the eager-vs-lazy comparison of Section 6.4).
 
 --impl reference times the CPU oracle (single-threaded Dijkstra) on the same workload
 and metric, one bounded sample per step.
@@ -54,7 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="road-sssp",
                    choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf",
-                            "rmat-kcore"])
+                            "rmat-kcore", "road-lazy", "rmat-lazy"])
     p.add_argument("--side", type=int, default=4900, help="road-like grid side")
     p.add_argument("--scale", type=int, default=24, help="R-MAT scale")
     p.add_argument("--sources", type=int, default=8)
@@ -223,7 +225,7 @@ def algo_bytes(m_r: int, n_r: int, n: int) -> int:
 
 def build_workload(args, rank, world):
     import graphgen
-    if args.workload in ("road-sssp", "serve", "road-bf"):
+    if args.workload in ("road-sssp", "serve", "road-bf", "road-lazy"):
         side = args.side
         g = graphgen.road(side, 0.15, 0.02, seed=1)
         name = f"road-like {side}x{side} grid"
@@ -256,7 +258,14 @@ def run_ours(args):
     G = og.Graph.from_csr(g)
     kind = {"rmat-wbfs": og.Q_WBFS, "road-bf": og.Q_BF}.get(args.workload, og.Q_SSSP)
     cfg = None
-    if not args.no_autotune and kind == og.Q_SSSP and not args.delta:
+    # eager-vs-lazy comparison (Section 6.4): both with the schedule that suits the graph
+    eager_ref = {"road-lazy": og.config(delta=4096, fusion_threshold=1024, expand_tile=32),
+                 "rmat-lazy": og.config(delta=256, fusion_threshold=og.FUSION_OFF,
+                                        expand_tile=256, hub_degree=1024)}.get(args.workload)
+    if eager_ref is not None:
+        cfg = og.config(delta=eager_ref.delta, expand_tile=eager_ref.expand_tile,
+                        hub_degree=eager_ref.hub_degree, bucket_update=og.UPDATE_LAZY)
+    elif not args.no_autotune and kind == og.Q_SSSP and not args.delta:
         lo, hi = (1 << 8, 1 << 16)
         cfg = og.autotune(G, kind, srcs, None, lo, hi)
     elif args.delta or args.fusion:
@@ -325,6 +334,20 @@ def run_ours(args):
                 "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": round(kernel_s * 1e3, 3)}
 
+    eager = None
+    if eager_ref is not None:
+        og.batch_run(G, queries, cfg=eager_ref, out=dbuf)
+        best = None
+        for _ in range(3):
+            _, _, est = og.batch_run(G, queries, cfg=eager_ref, out=dbuf)
+            if best is None or est.kernel_ns < best.kernel_ns:
+                best = est
+        eager = {"schedule": {"delta": int(eager_ref.delta),
+                              "fusion_threshold": int(eager_ref.fusion_threshold),
+                              "expand_tile": int(eager_ref.expand_tile)},
+                 "kernel_ms": round(best.kernel_ns / 1e6, 3), "rounds": int(best.rounds),
+                 "inserts": int(best.global_inserts + best.local_inserts + best.overflow_inserts),
+                 "eager_speedup": round(kernel_s * 1e9 / best.kernel_ns, 2)}
     ordered = None
     if kind == og.Q_BF:
         # the same sources by the ordered method (Delta-stepping with fusion), same GPU
@@ -348,10 +371,13 @@ def run_ours(args):
     if rank == 0:
         value = m_r * world / step_s / 1e9
         kname = {og.Q_SSSP: "SSSP", og.Q_WBFS: "wBFS", og.Q_BF: "Bellman-Ford"}[kind]
+        metric = {og.Q_SSSP: "SSSP GTEPS (Delta-stepping with bucket fusion)",
+                  og.Q_WBFS: "wBFS GTEPS",
+                  og.Q_BF: "SSSP GTEPS (unordered Bellman-Ford baseline)"}[kind]
+        if eager is not None:
+            metric = "SSSP GTEPS (Delta-stepping with the lazy bucket update)"
         line = {
-            "metric": {og.Q_SSSP: "SSSP GTEPS (Delta-stepping with bucket fusion)",
-                       og.Q_WBFS: "wBFS GTEPS",
-                       og.Q_BF: "SSSP GTEPS (unordered Bellman-Ford baseline)"}[kind],
+            "metric": metric,
             "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(step_s * 1e3, 3), "higher_is_better": True,
@@ -366,6 +392,7 @@ def run_ours(args):
                        "hub_degree": int(eff.hub_degree),
                        "blocks_per_sm": int(eff.blocks_per_sm),
                        "engine": "async" if int(eff.engine) == 2 else "rounds",
+                       "bucket_update": "lazy" if int(eff.bucket_update) == 2 else "eager",
                        "l2": "inputs larger than L2 (graph %.0f MB + dist %.0f MB > 129 MB)"
                              % ((8 * g.m + 4 * g.n) / 1e6, 4 * nq * g.n / 1e6),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -378,6 +405,8 @@ def run_ours(args):
         }
         if ordered is not None:
             line["ordered"] = ordered
+        if eager is not None:
+            line["eager"] = eager
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -656,6 +685,7 @@ def run_kcore(args):
     torch.cuda.init()
     g = graphgen.rmat(args.scale, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
     G = og.Graph.from_csr(g)
+    G.set_config(og.config(hub_degree=args.hub, expand_tile=args.tile))
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     core, st0 = og.kcore(G, og.KCORE_LAZY, out=out)
     ref_core = out.cpu().numpy().view(np.uint32).copy()
@@ -713,6 +743,8 @@ def run_kcore(args):
         "config": {"workload": f"R-MAT scale {args.scale} k-core (coreness of every vertex), "
                                "one persistent launch per step", "n": g.n, "m": g.m,
                    "max_coreness": int(ref_core.max()),
+                   "hub_degree": int(G.get_config().hub_degree),
+                   "expand_tile": int(G.get_config().expand_tile),
                    "l2": "inputs larger than L2 (graph %.0f MB)" % (8 * g.m / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),
                      "peak": peak, "unit": "GB/s",

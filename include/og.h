@@ -91,11 +91,20 @@ typedef struct og_config {
                                 are split over every warp of the grid in a pass after
                                 the round (round engine, CSR layout; 0 = default 4096,
                                 0xFFFFFFFF = no hubs)                                  */
+  uint32_t bucket_update;    /* OG_UPDATE_EAGER (Section 3.2; 0 = default) or
+                                OG_UPDATE_LAZY (Section 3.1): a round only relaxes and
+                                marks each improved vertex once; after the round every
+                                marked vertex makes one insertion, into the bucket of
+                                its final distance (the buffer reduction).  Lazy turns
+                                fusion off and runs on the round engine.                */
+  uint32_t reserved2;
   uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
   uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
 } og_config;
 
 #define OG_FUSION_OFF 0xFFFFFFFEu
+#define OG_UPDATE_EAGER 1u
+#define OG_UPDATE_LAZY 2u
 
 /* Engines.  Both run the same eager Delta-stepping with bucket fusion and give the same
  * distances.  ROUNDS (the default) follows the paper's round structure: every CTA fuses
@@ -203,8 +212,9 @@ int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats
  *         vertex and round; OG_KCORE_EAGER -- eager update (Section 3.2): one
  *         compare-and-swap decrement and one bucket insertion per edge.
  *   cfg: NULL or a config; used fields: expand_tile (frontier entries per claim, rounded
- *        up to 256), hub_degree (frontier vertices of at least this out-degree have
- *        their edges split over every warp of the grid), blocks_per_sm, spin_limit_ns,
+ *        up to 256; a small frontier gets smaller tiles), hub_degree (frontier vertices
+ *        of at least this out-degree have their edges split over every warp of the grid;
+ *        0 = 256 here), blocks_per_sm, spin_limit_ns,
  *        arena_entries (vertex ids held by the
  *        256 materialised buckets; default 4n; a bucket that runs out of space is rebuilt
  *        by a scan at its level, so any size gives the same result).

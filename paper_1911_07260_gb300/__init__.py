@@ -29,6 +29,7 @@ PRECHECK_ON, PRECHECK_OFF = 1, 2
 LAYOUT_CSR, LAYOUT_ELL = 1, 2
 PREFETCH_ON, PREFETCH_OFF = 1, 2
 KCORE_LAZY, KCORE_EAGER = 0, 1
+UPDATE_EAGER, UPDATE_LAZY = 1, 2
 UNREACHED = 0xFFFFFFFF
 
 
@@ -47,6 +48,7 @@ class Config(ctypes.Structure):
                 ("ring_buckets", ctypes.c_uint32), ("engine", ctypes.c_uint32),
                 ("precheck", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("prefetch", ctypes.c_uint32), ("hub_degree", ctypes.c_uint32),
+                ("bucket_update", ctypes.c_uint32), ("reserved2", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("arena_entries", ctypes.c_uint64)]
 
     def as_dict(self):

@@ -112,6 +112,7 @@ struct HBuf {
 struct Workspace {
   DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big, bmap;
   DBuf kprio, kcnt, ktouched, klist, kring, kcounts, klossy, kstate;  // k-core
+  DBuf lzbits, lzlist;  // lazy bucket update
   HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq, h_kstate;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // Barrier-free engine: ring positions must read "free" (all ones) before use.  Entries
@@ -122,7 +123,7 @@ struct Workspace {
   void release() {
     for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
                     &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
-                    &kstate})
+                    &kstate, &lzbits, &lzlist})
       b->release();
     for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq, &h_kstate}) b->release();
     clean_upto = 0;
@@ -170,6 +171,7 @@ constexpr uint32_t kBinCap = 2048;
 constexpr uint32_t kDefaultHub = 4096;      // out-degree from which a vertex is a hub
 constexpr uint32_t kHubSlots = 65536;       // hubs listed per round
 constexpr uint32_t kHubChunks = 1u << 20;   // 1024-edge hub chunks per round
+constexpr uint32_t kKcoreHub = 256;         // k-core: default hub out-degree
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 
 }  // namespace
@@ -240,6 +242,7 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.blocks_per_sm = pick32(u.blocks_per_sm, g->cfg.blocks_per_sm, 0);
   r.ring_buckets = pick32(u.ring_buckets, g->cfg.ring_buckets, 0);
   r.hub_degree = pick32(u.hub_degree, g->cfg.hub_degree, kDefaultHub);
+  r.bucket_update = pick32(u.bucket_update, g->cfg.bucket_update, OG_UPDATE_EAGER);
   r.spin_limit_ns = pick64(u.spin_limit_ns, g->cfg.spin_limit_ns, kDefaultSpinNs);
   r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
   r.engine = u.engine ? u.engine : g->cfg.engine;
@@ -384,6 +387,20 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     P.precheck = c.precheck == OG_PRECHECK_ON ? 1u : 0u;
     P.prefetch = c.prefetch == OG_PREFETCH_OFF ? 0u : 1u;
     P.spin_ns = c.spin_limit_ns;
+    if (c.bucket_update == OG_UPDATE_LAZY) {  // marks instead of inserts; no fusion
+      const uint32_t words = (g->n + 31) / 32;
+      // One mark per (vertex, query) and round; at most 2^28 marks a round (2 GB).
+      const uint32_t lz_cap = (uint32_t)std::min<uint64_t>((uint64_t)nq * g->n, 1ull << 28);
+      TRY(ws.lzbits.ensure(sizeof(uint32_t) * (size_t)nq * words));
+      TRY(ws.lzlist.ensure(sizeof(uint2) * (size_t)lz_cap));
+      CK(cudaMemsetAsync(ws.lzbits.p, 0, sizeof(uint32_t) * (size_t)nq * words, st));
+      P.lazy = 1u;
+      P.T = 0u;
+      P.lz_words = words;
+      P.lz_bits = ws.lzbits.as<uint32_t>();
+      P.lz_list = ws.lzlist.as<uint2>();
+      P.lz_cap = lz_cap;
+    }
 
     CK(cudaMemcpyAsync(ws.qd.p, ws.h_qd.p, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ws.slots.p, ws.h_slots.p, sizeof(uint32_t) * np,
@@ -615,7 +632,8 @@ int run_chunk(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og
               uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
   bool bf = false;
   for (uint32_t i = 0; i < nq; ++i) bf |= qd[i].kind == kBF;
-  if (c.engine == OG_ENGINE_ASYNC && !bf)  // Bellman-Ford rounds need the round engine
+  // Bellman-Ford rounds and the lazy bucket update need the round engine.
+  if (c.engine == OG_ENGINE_ASYNC && !bf && c.bucket_update != OG_UPDATE_LAZY)
     return run_chunk_async(g, ws, qd, nq, c, dist_dev, d_out, acc, ro, st);
   return run_chunk_rounds(g, ws, qd, nq, c, dist_dev, d_out, acc, ro, st);
 }
@@ -967,7 +985,13 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   P.ks = ws.kstate.as<KState>();
   P.stats = ws.stats.as<Stats>();
   // Hubs (out-degree >= hub_degree) are split over every warp after the round's peel.
-  const uint32_t hub_cap = g->max_deg >= c.hub_degree ? kHubSlots : 0u;
+  // Unset, the threshold is lower than for Delta-stepping: a peeling round has one
+  // frontier and no fused levels, so moving its long adjacency lists to the balanced hub
+  // pass costs little (R-MAT-24, lazy: 100 ms at 4096, 82 ms at 256).
+  const uint32_t hub_min = (ucfg && ucfg->hub_degree) ? ucfg->hub_degree
+                           : g->cfg.hub_degree        ? g->cfg.hub_degree
+                                                      : kKcoreHub;
+  const uint32_t hub_cap = g->max_deg >= hub_min ? kHubSlots : 0u;
   if (hub_cap) {
     TRY(ws.big.ensure(sizeof(BigItem) * hub_cap));
     TRY(ws.bmap.ensure(sizeof(uint32_t) * kHubChunks));
@@ -976,7 +1000,7 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   P.hub_map = hub_cap ? ws.bmap.as<uint32_t>() : nullptr;
   P.hub_cap = hub_cap;
   P.map_cap = hub_cap ? kHubChunks : 0u;
-  P.hub_min = c.hub_degree;
+  P.hub_min = hub_min;
   P.cap = (uint32_t)cap64;
   P.eager = mode == OG_KCORE_EAGER ? 1u : 0u;
   P.tile = std::max<uint32_t>(kBlock, (c.expand_tile + kBlock - 1) / kBlock * kBlock);
@@ -1049,6 +1073,10 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   if (!s) return OG_E_OOM;
   s->g = g;
   s->cfg = resolve(g, cfg);
+  if (s->cfg.bucket_update == OG_UPDATE_LAZY) {  // the server runs the barrier-free engine
+    delete s;
+    return OG_E_INVALID;
+  }
   s->stream = (cudaStream_t)stream;
   const uint32_t B = ring_size(g, s->cfg, s->cfg.delta);
   const uint64_t entries = s->cfg.arena_entries

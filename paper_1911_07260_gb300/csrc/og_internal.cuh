@@ -35,6 +35,7 @@ enum Phase : uint32_t {
   kPhStop = 3,
   kPhPrologue = 4,   // kernel start: publish the frontier of the current state
   kPhBig = 5,        // edges of very-high-degree vertices, split over all CTAs
+  kPhApply = 6,      // lazy bucket update: one insertion per vertex marked this round
 };
 
 // A vertex whose out-degree is at least Params::hub_min (a hub of a skewed graph) is not
@@ -90,7 +91,7 @@ struct Sync {
   uint32_t bad_aux;      // context (query or position)
   uint32_t progress;     // barrier-free engine: heartbeat of busy warps
   uint32_t timeout_at;   // which bounded wait gave up (1 idle, 2 entry hand-off)
-  uint32_t pad[1];
+  uint32_t lz_n;         // lazy bucket update: vertices marked this round
   unsigned long long big_word;  // (listed hubs << 32) | chunks reserved, this round
 };
 
@@ -135,6 +136,11 @@ struct Params {
   uint32_t has_astar;
   uint32_t precheck;      // load dist[v] first; atomicMin only if the new value is smaller
   uint32_t prefetch;      // prefetch an inserted vertex's adjacency into L2
+  uint32_t lazy;          // lazy bucket update (Section 3.1) instead of eager inserts
+  uint32_t lz_words;      // words per query of the marked-vertex bitmap
+  uint32_t* lz_bits;      // nq x lz_words: vertex improved this round
+  uint2* lz_list;         // {vertex, query} marked this round
+  uint32_t lz_cap;
   unsigned long long spin_ns;
 };
 

@@ -221,16 +221,19 @@ __device__ void peel_phase(const KParams& P, KSmem& S, KCnt& C) {
   const uint32_t k = S.k, total = S.fr_n;
   const uint32_t* fr = S.fr_list ? P.list[S.fsel] : P.ring + (size_t)S.cur * P.cap;
   const uint32_t* nb = reinterpret_cast<const uint32_t*>(P.adj);  // .x of {nbr, w}
+  // A small frontier is spread over all CTAs: the tile shrinks to about total / grid.
+  const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
+  const uint32_t tile = min(P.tile, max(32u, (per + 31u) & ~31u));
   for (;;) {
-    if (tid == 0) S.grab = atomicAdd(&P.sync->work, P.tile);
+    if (tid == 0) S.grab = atomicAdd(&P.sync->work, tile);
     __syncthreads();
     const uint32_t base = S.grab;
     __syncthreads();
     if (base >= total) break;
-    for (uint32_t k0 = 0; k0 < P.tile; k0 += kBlock) {
+    for (uint32_t k0 = 0; k0 < tile; k0 += kBlock) {
       const uint32_t i = base + k0 + tid;
       uint32_t beg = 0, deg = 0;
-      if (k0 + tid < P.tile && i < total) {
+      if (k0 + tid < tile && i < total) {
         const uint32_t u = __ldcg(fr + i);
         if (u < P.n) {
           C.items++;

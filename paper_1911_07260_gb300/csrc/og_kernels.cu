@@ -112,6 +112,21 @@ __device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins
   }
 }
 
+// Lazy bucket update: appends {vertex, query} of the lanes with first (the vertex's first
+// improvement this round) to the round's list, warp-aggregated.  All 32 lanes call it.
+__device__ __forceinline__ void mark_warp(const Params& P, bool first, uint32_t v, uint32_t q) {
+  const unsigned m = __ballot_sync(FULL, first);
+  if (m == 0u) return;
+  const int leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&P.sync->lz_n, (uint32_t)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (!first) return;
+  const uint32_t pos = base + __popc(m & lanemask_lt());
+  if (pos < P.lz_cap) P.lz_list[pos] = make_uint2(v, q);
+  else report_bad(P.sync, 41u, v, q);  // more marks in one round than the list holds
+}
+
 // Relaxes up to K edges per lane: nd = g + w (saturating), atomicMin on dist[v]; an
 // improvement is inserted eagerly into bucket floor((nd + h) / Delta).  All K neighbor
 // loads are issued before any atomic and all K atomics before any insert, so a lane keeps
@@ -156,6 +171,21 @@ __device__ __forceinline__ void relax_edges(const Params& P, Smem& S, const Bins
 #pragma unroll
   for (int k = 0; k < K; ++k)
     old[k] = go[k] ? atomicMin(P.dist + (size_t)q[k] * P.n + ew[k].x, nd[k]) : 0u;
+  if (P.lazy) {  // lazy bucket update: mark each improved vertex once this round
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ins = go[k] && nd[k] < old[k];
+      C.relax += ok[k] ? 1u : 0u;
+      C.improved += ins ? 1u : 0u;
+      bool first = false;
+      if (ins) {
+        const uint32_t bit = 1u << (ew[k].x & 31u);
+        first = (atomicOr(P.lz_bits + (size_t)q[k] * P.lz_words + (ew[k].x >> 5), bit) & bit) == 0u;
+      }
+      mark_warp(P, first, ew[k].x, q[k]);
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const bool ins = go[k] && nd[k] < old[k];
@@ -424,6 +454,18 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
       sy->big_word = 0ull;
       sy->big_claim = 0u;
     }
+    done_phase = kPhRelax;
+  }
+  if (done_phase == kPhRelax && !fatal && P.lazy && __ldcg(&sy->lz_n) > 0u) {
+    // Lazy bucket update: the marked vertices make their insertions before the round ends.
+    if (tid == 0) {
+      sy->phase = kPhApply;
+      sy->work = 0;
+    }
+    return;
+  }
+  if (done_phase == kPhApply) {
+    if (tid == 0) sy->lz_n = 0u;
     done_phase = kPhRelax;
   }
   if (tid == 0) {
@@ -793,6 +835,40 @@ __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   if (tid == 0) S.t_hub += gtimer() - t_start;
 }
 
+// The lazy bucket update's reduction (Section 3.1): every vertex marked this round is
+// inserted once, into the bucket of its distance now (the minimum of the round's
+// updates); its mark is cleared for the next round.
+__device__ void lazy_apply_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
+  __syncthreads();
+  const uint32_t tn = min(__ldcg(&P.sync->lz_n), P.lz_cap);
+  for (uint32_t i0 = blockIdx.x * kBlock; i0 < tn; i0 += gridDim.x * kBlock) {
+    const uint32_t i = i0 + tid;
+    bool has = i < tn;
+    uint32_t v = 0, q = 0, d = 0, key = 0;
+    if (has) {
+      const uint2 en = __ldcg(P.lz_list + i);
+      v = en.x;
+      q = en.y;
+      if (v < P.n && q < P.nq) {
+        atomicAnd(P.lz_bits + (size_t)q * P.lz_words + (v >> 5), ~(1u << (v & 31u)));
+        d = __ldcg(P.dist + (size_t)q * P.n + v);
+        const QDesc* qd = P.qd + q;
+        const uint32_t h = (P.has_astar && __ldg(&qd->kind) == kASTAR)
+                               ? heuristic(P.xy, P.xy_integral, v, __ldg(&qd->tx), __ldg(&qd->ty))
+                               : 0u;
+        const uint32_t dq = S.delta[q];
+        key = dq ? bucket_of(d, h, dq) : S.cur[q] + 1u;
+      } else {
+        report_bad(P.sync, 42u, v, q);
+        has = false;
+      }
+    }
+    insert_warp(P, S, B, 0, has, false, v, d, key, q, C);
+  }
+}
+
 template <bool ELL>
 __device__ __forceinline__ void delta_body(const Params& P) {
   extern __shared__ __align__(16) unsigned char og_dyn_smem[];
@@ -814,6 +890,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
     if (phase == kPhRelax) relax_phase<ELL>(P, S, B, C, fused);
     else if (phase == kPhRedistMin) redist_min_phase(P);
     else if (phase == kPhRedistMove) redist_move_phase(P);
+    else if (phase == kPhApply) lazy_apply_phase(P, S, B, C);
     else if (phase == kPhBig) {
       if constexpr (!ELL) big_phase(P, S, B, C);  // ELL rows hold <= 8 edges: no hubs
     }

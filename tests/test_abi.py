@@ -44,7 +44,7 @@ def test_binding_fails_loudly_without_library(og, monkeypatch, tmp_path):
 
 def test_structs_match_header(og):
     # og_config: 10 x uint32 + 2 x uint64; og_stats: 16 x uint64; og_query: 4 x uint32
-    assert ctypes.sizeof(og.Config) == 56
+    assert ctypes.sizeof(og.Config) == 64
     assert ctypes.sizeof(og.Stats) == 136
     assert ctypes.sizeof(og.Query) == 16
 

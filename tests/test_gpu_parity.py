@@ -579,3 +579,41 @@ def test_kcore_hub_pass(og, orc, gg, mode, hub):
     g = _sym_pairs(gg, n, p)
     got, _ = og.kcore(og.Graph.from_csr(g), mode, cfg=cfg)
     np.testing.assert_array_equal(got, orc.kcore(g))
+
+
+@pytest.mark.parametrize("delta", [1, 37, 1000, 1 << 20])
+def test_lazy_bucket_update_matches_oracle(og, orc, gg, grid256, delta):
+    """The lazy bucket update (Section 3.1: relax, mark each improved vertex once, then
+    one insertion per marked vertex into the bucket of its final distance) reaches the
+    oracle's distances for SSSP on the grid and R-MAT, makes at most one insertion per
+    improvement and fuses nothing; the asynchronous engine request falls back to rounds."""
+    g, G = grid256
+    cfg = og.config(delta=delta, bucket_update=og.UPDATE_LAZY, engine=og.ENGINE_ASYNC)
+    for s in (0, 40000):
+        got, _, st = og.query_run(G, og.Q_SSSP, s, cfg=cfg)
+        np.testing.assert_array_equal(got, orc.dijkstra(g, s))
+        assert st.fused_iters == 0 and st.local_inserts == 0
+        assert st.global_inserts + st.overflow_inserts <= st.improved
+    r = gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1 << 16, seed=5)
+    R = og.Graph.from_csr(r)
+    for s in gg.sample_sources(r, 2, seed=3):
+        got, _, _ = og.query_run(R, og.Q_SSSP, int(s), cfg=og.config(delta=delta * 64,
+                                 bucket_update=og.UPDATE_LAZY, hub_degree=64))
+        np.testing.assert_array_equal(got, orc.dijkstra(r, int(s)))
+
+
+def test_lazy_bucket_update_batches_ppsp_astar(og, orc, gg, road300):
+    """Lazy batches mixing SSSP, PPSP, A*, wBFS-like Delta 1 and Bellman-Ford stay exact;
+    the server refuses a lazy schedule."""
+    g, G = road300
+    s = [int(x) for x in gg.sample_sources(g, 6, seed=13)]
+    qs = [(og.Q_SSSP, s[0], 0, 512), (og.Q_PPSP, s[1], s[2], 1024),
+          (og.Q_ASTAR, s[3], s[4], 2048), (og.Q_SSSP, s[5], 0, 1), (og.Q_BF, s[2], 0, 0)]
+    out, d, _ = og.batch_run(G, qs, cfg=og.config(bucket_update=og.UPDATE_LAZY))
+    out = out.reshape(len(qs), g.n)
+    for i in (0, 3, 4):
+        np.testing.assert_array_equal(out[i], orc.dijkstra(g, qs[i][1]))
+    assert d[1] == orc.ppsp(g, s[1], s[2]) and d[2] == orc.ppsp(g, s[3], s[4])
+    with pytest.raises(og.OgError) as e:
+        og.Server(G, max_slots=4, cfg=og.config(bucket_update=og.UPDATE_LAZY))
+    assert e.value.code == og.E_INVALID
