@@ -16,6 +16,12 @@
 //   * between rounds a bounded grid barrier runs; the CTA that arrives last picks the
 //     next bucket of every query (the smallest non-empty one, scanned with a warp ballot)
 //     and applies the PPSP / A* stop rule before it releases the others.
+// Within a round: frontier tiles are expanded CTA-wide and edge-balanced (expand_cta),
+// fused levels per warp (expand_warp); vertices of out-degree >= hub_degree are listed
+// and their edges split over every warp after the frontier pass (BIG phase).  Two more
+// modes share the kernel: the lazy bucket update (Section 3.1: marks during the round,
+// one insertion per marked vertex in the APPLY phase) and unordered Bellman-Ford
+// (QDesc.delta = 0: every improvement goes to bucket cur + 1).
 #include "og_device.cuh"
 
 namespace og {
