@@ -75,7 +75,7 @@ def parse_args(argv=None):
     p.add_argument("--rates", type=float, nargs="+", default=[10000.0],
                    help="serve: Poisson arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=128, help="serve: resident query slots")
-    p.add_argument("--budget-us", type=int, default=200, help="serve: time per launch")
+    p.add_argument("--budget-us", type=int, default=400, help="serve: time per launch")
     p.add_argument("--serve-fusion", type=int, default=64, help="serve: fusion threshold")
     p.add_argument("--sequential", type=int, default=2000,
                    help="serve: queries in the one-at-a-time baseline")
