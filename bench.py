@@ -604,7 +604,10 @@ def run_batch(args):
         "config": {"workload": "road-like 1024x1024 grid, 256 queries in one persistent launch",
                    "n": g.n, "m": g.m, "delta": int(cfg.delta),
                    "fusion_threshold": int(cfg.fusion_threshold),
-                   "expand_tile": int(cfg.expand_tile), "engine": int(cfg.engine)},
+                   "expand_tile": int(cfg.expand_tile), "engine": int(cfg.engine),
+                   "blocks_per_sm": int(cfg.blocks_per_sm), "precheck": int(cfg.precheck),
+                   "prefetch": int(cfg.prefetch), "hub_degree": int(cfg.hub_degree),
+                   "layout": "ell" if int(cfg.layout) == 2 else "csr"},
         "one_at_a_time": {"value": round(nq / single_s, 2), "unit": "queries/s",
                           "schedule": {"delta": int(cfg1.delta),
                                        "fusion_threshold": int(cfg1.fusion_threshold),

@@ -415,7 +415,10 @@ __device__ void advance(const AParams& P, uint32_t q) {
 }
 
 // Adds delta (two's complement) to a query's outstanding count; advances the query if
-// it reached zero.
+// it reached zero.  Every lane fences before lane 0 settles: the lanes' earlier stores
+// (a consumed ring position reset to free, entries appended) must be visible before the
+// count can reach zero, because reaching zero lets the query advance and reuse the ring
+// slot; a reset arriving after a new entry in the reused slot would erase that entry.
 __device__ __forceinline__ void settle(const AParams& P, uint32_t q, uint32_t delta) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t zero = 0;
@@ -423,8 +426,9 @@ __device__ __forceinline__ void settle(const AParams& P, uint32_t q, uint32_t de
     if (lane == 0) report_bad(P.sync, 8u, q, delta);
     return;
   }
+  __threadfence();
+  __syncwarp();
   if (lane == 0 && delta != 0) {
-    __threadfence();
     const uint32_t old = atomicAdd(&P.aq[q].work, delta);
     zero = (old + delta == 0u) ? 1u : 0u;
   }
