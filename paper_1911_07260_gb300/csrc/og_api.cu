@@ -1189,6 +1189,7 @@ int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active) {
     s->pending.clear();
   }
   CK(cudaMemsetAsync(&ws.sync.as<Sync>()->err, 0, sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(ws.stats.p, 0, sizeof(Stats), st));  // counters and wait diagnostics
   const int bps = s->cfg.blocks_per_sm ? std::min<int>((int)s->cfg.blocks_per_sm, g->occ_async)
                                        : g->occ_async;
   CK(launch_async(P, g->sms * bps, smem, st));
@@ -1203,8 +1204,20 @@ int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active) {
     return OG_E_INTERNAL;
   }
   if (hy->err & kErrTimeout) {
-    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s wait gave up",
-             hy->timeout_at == 2u ? "entry hand-off" : "idle (no progress)");
+    if (hy->timeout_at == 2u) {
+      Stats hs;
+      CK(cudaMemcpy(&hs, ws.stats.p, sizeof(Stats), cudaMemcpyDeviceToHost));
+      const unsigned long long a = hs.v[kStTFrontier], b = hs.v[kStTFused],
+                               w = hs.v[kStTBarrier], c = hs.v[kStTHub];
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg),
+               "entry hand-off wait gave up: query %u position %u, bucket %u with %u "
+               "appends, claim word epoch %u position %u, query cursor %u mode %u count %u",
+               (uint32_t)(a >> 32), (uint32_t)a, (uint32_t)(b >> 32), (uint32_t)b,
+               (uint32_t)(w >> 32), (uint32_t)w, (uint32_t)(c >> 32),
+               (uint32_t)((c >> 28) & 0xFu), (uint32_t)(c & 0x0FFFFFFFu));
+    } else {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "idle wait gave up (no progress)");
+    }
     return OG_E_TIMEOUT;
   }
   const AQState* ha = ws.h_aq.as<AQState>();

@@ -660,6 +660,20 @@ __device__ __forceinline__ void async_body(const AParams& P) {
           while ((uint32_t)x == 0xFFFFFFFFu) {  // reserved, not yet written
             if ((++spins & 63u) == 0 && gtimer() - t0 > P.spin_ns) {
               P.sync->timeout_at = 2u;
+              // Where the wait gave up, for the error message (the timer slots of the
+              // statistics are unused by this engine): query and position, bucket and
+              // its append count, the claim word, the query's cursor / mode / count.
+              const AQState* aq = P.aq + q;
+              const unsigned long long where = ((unsigned long long)q << 32) | (start + lane);
+              if (atomicCAS(&P.stats->v[kStTFrontier], 0ull, where) == 0ull) {
+                P.stats->v[kStTFused] =
+                    ((unsigned long long)cur << 32) |
+                    __ldcg(P.counts + (size_t)q * P.B + (cur & P.Bmask));
+                P.stats->v[kStTBarrier] = ld_relaxed64(&aq->word);
+                P.stats->v[kStTHub] = ((unsigned long long)__ldcg(&aq->cur) << 32) |
+                                      ((unsigned long long)__ldcg(&aq->mode) << 28) |
+                                      (__ldcg(&aq->work) & 0x0FFFFFFFu);
+              }
               atomicOr(&P.sync->err, kErrTimeout);
               break;
             }
