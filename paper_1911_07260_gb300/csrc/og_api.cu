@@ -1119,7 +1119,15 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   if (r == OG_OK) r = ws.h_sync.ensure(sizeof(Sync));
   if (r == OG_OK) r = ws.h_slots.ensure(sizeof(uint32_t) * slots);
   if (r == OG_OK) r = ws.events();
-  if (r == OG_OK && cudaMemsetAsync(ws.aq.p, 0, sizeof(AQState) * slots, s->stream) != cudaSuccess)
+  // A slot without a query must offer nothing to claim: all-ones makes its claim word
+  // closed.  The bucket counters start at zero.  (Device memory comes back uncleared
+  // from an earlier server; zeroed states read as an open word over stale counters, and
+  // idle warps then waited for entries that were never written.)
+  if (r == OG_OK &&
+      cudaMemsetAsync(ws.aq.p, 0xFF, sizeof(AQState) * slots, s->stream) != cudaSuccess)
+    r = OG_E_CUDA;
+  if (r == OG_OK && cudaMemsetAsync(ws.counts.p, 0, sizeof(uint32_t) * (size_t)slots * B,
+                                    s->stream) != cudaSuccess)
     r = OG_E_CUDA;
   if (r == OG_OK && cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), s->stream) != cudaSuccess)
     r = OG_E_CUDA;

@@ -617,3 +617,30 @@ def test_lazy_bucket_update_batches_ppsp_astar(og, orc, gg, road300):
     with pytest.raises(og.OgError) as e:
         og.Server(G, max_slots=4, cfg=og.config(bucket_update=og.UPDATE_LAZY))
     assert e.value.code == og.E_INVALID
+
+
+def test_server_on_recycled_device_memory(og, orc, gg, road300):
+    """A server whose buffers come back from freed device memory holding junk must offer
+    nothing to claim in its idle slots: device memory is filled with a non-zero pattern
+    and released first, then a 64-slot server answers 3 queries exactly, with a short
+    wait limit so that a claim on a query-less slot would fail fast."""
+    import torch
+    g, G = road300
+    junk = torch.full((1 << 28,), 0x00000F00, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    del junk
+    torch.cuda.empty_cache()
+    pairs = gg.sample_pairs_grid_steps(g, 3, 10, 200, seed=5)
+    srv = og.Server(G, max_slots=64, cfg=og.config(delta=512, fusion_threshold=64,
+                                                      spin_limit_ns=200_000_000))
+    for i, (s, t) in enumerate(pairs.tolist()):
+        assert srv.submit(og.Q_PPSP, int(s), int(t), tag=i)
+    got = {}
+    for _ in range(10000):
+        srv.step(budget_us=200)
+        tags, d = srv.poll()
+        got.update({int(a): int(b) for a, b in zip(tags, d)})
+        if len(got) == len(pairs):
+            break
+    srv.free()
+    assert got == {i: orc.ppsp(g, int(s), int(t)) for i, (s, t) in enumerate(pairs.tolist())}
