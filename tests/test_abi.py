@@ -43,10 +43,40 @@ def test_binding_fails_loudly_without_library(og, monkeypatch, tmp_path):
 
 
 def test_structs_match_header(og):
-    # og_config: 10 x uint32 + 2 x uint64; og_stats: 16 x uint64; og_query: 4 x uint32
+    # og_config: 12 x uint32 + 2 x uint64; og_stats: 17 x uint64; og_query: 4 x uint32
     assert ctypes.sizeof(og.Config) == 64
     assert ctypes.sizeof(og.Stats) == 136
     assert ctypes.sizeof(og.Query) == 16
+
+
+def _header():
+    here = os.path.dirname(os.path.abspath(__file__))
+    return open(os.path.join(here, "..", "include", "og.h")).read()
+
+
+def test_constants_match_header_defines(og):
+    """Every #define OG_<NAME> <number> of the header has the same value in the binding
+    (OG_E_X -> E_X, OG_OK -> OK, OG_Q_X -> Q_X, OG_FUSION_OFF -> FUSION_OFF, ...)."""
+    import re
+    defs = dict(re.findall(r"^#define OG_([A-Z0-9_]+)\s+(0x[0-9A-Fa-f]+|[0-9]+)u?\b", _header(),
+                           re.M))
+    assert len(defs) >= 25
+    for name, val in defs.items():
+        assert hasattr(og, name), f"binding lacks {name}"
+        assert getattr(og, name) == int(val, 0), name
+
+
+def test_struct_fields_match_header(og):
+    """The binding's Config / Stats / Query fields are the header's, in the same order."""
+    import re
+    text = _header()
+    for cname, py in (("og_config", og.Config), ("og_stats", og.Stats), ("og_query", og.Query)):
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (cname, cname), text, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"uint(32|64)_t\s+(\w+);", body)
+        assert [n for _, n in fields] == [n for n, _ in py._fields_], cname
+        for (bits, n), (pn, pt) in zip(fields, py._fields_):
+            assert ctypes.sizeof(pt) * 8 == int(bits), (cname, n)
 
 
 def test_library_does_not_link_the_oracle(og):
