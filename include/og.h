@@ -6,8 +6,10 @@
  * fusion (Section 3.2, "Eager Bucket Update", and Section 3.3, "Eager Bucket Fusion
  * Optimization", with the figure "SSSP with the eager bucket update approach and the
  * bucket fusion optimization").  Weighted BFS, PPSP and A* are variants of the same
- * loop (Section 6.1, "Applications").  Every step runs in CUDA kernels for sm_103a; there
- * is no CPU fallback.
+ * loop (Section 6.1, "Applications").  The lazy bucket update (Section 3.1), the
+ * unordered Bellman-Ford baseline and k-core by peeling (Section 6.1, lazy with the
+ * constant-sum reduction of Section 5.1, or eager) complete the comparisons of Section
+ * 6.4.  Every step runs in CUDA kernels for sm_103a; there is no CPU fallback.
  *
  * Conventions shared by every entry point
  *   - Vertices are uint32 ids in [0, n).  Weights are non-negative uint32.
