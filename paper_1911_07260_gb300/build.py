@@ -17,6 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libog.so")
 SOURCES = ["og_kernels.cu", "og_async.cu", "og_kcore.cu", "og_api.cu"]
 HEADERS = [os.path.join(CSRC, "og_internal.cuh"), os.path.join(CSRC, "og_device.cuh"),
+           os.path.join(CSRC, "og_kcore.cuh"),
            os.path.join(INCLUDE, "og.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,6 +17,7 @@
 
 #include "og.h"
 #include "og_internal.cuh"
+#include "og_kcore.cuh"
 
 namespace og {
 cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st);
@@ -957,7 +958,7 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   const uint64_t cap64 = std::max<uint64_t>(1024, entries / kKRing);
   if (cap64 >= 0xFFFFFFF0ull) return OG_E_INVALID;
   TRY(ws.kcnt.ensure(sizeof(uint32_t) * (size_t)n));
-  TRY(ws.ktouched.ensure(sizeof(uint32_t) * (size_t)n));
+  TRY(ws.ktouched.ensure(2 * sizeof(uint32_t) * (size_t)n));
   TRY(ws.klist.ensure(2 * sizeof(uint32_t) * (size_t)n));
   TRY(ws.kring.ensure(sizeof(uint32_t) * (size_t)kKRing * cap64));
   TRY(ws.kcounts.ensure(sizeof(uint32_t) * kKRing));
@@ -975,7 +976,8 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   P.n = n;
   P.prio = prio;
   P.cnt = ws.kcnt.as<uint32_t>();
-  P.touched = ws.ktouched.as<uint32_t>();
+  P.touched[0] = ws.ktouched.as<uint32_t>();
+  P.touched[1] = P.touched[0] + n;
   P.list[0] = ws.klist.as<uint32_t>();
   P.list[1] = P.list[0] + n;
   P.ring = ws.kring.as<uint32_t>();

@@ -16,6 +16,7 @@
 // One cooperative persistent launch; phases are separated by a bounded grid barrier whose
 // last arriver decides the next phase (kdecide).  The final priorities are the coreness.
 #include "og_device.cuh"
+#include "og_kcore.cuh"
 
 namespace og {
 
@@ -25,7 +26,7 @@ constexpr int kKBatch = 4;  // edges per thread per batch
 
 struct KSmem {
   uint32_t phase, err, last, grab;
-  uint32_t k, base, cur, fr_list, fsel, fr_n, asel;
+  uint32_t k, base, cur, fr_list, fsel, fr_n, asel, tsel;
   uint32_t lb_pos[kBlock + 1];  // edge prefix sums of a sub-tile's entries
   uint32_t lb_beg[kBlock];
   uint32_t wtmp[kWarps + 1];
@@ -132,7 +133,7 @@ __device__ __forceinline__ void update_batch(const KParams& P, const KSmem& S, K
     }
 #pragma unroll
     for (int b = 0; b < kKBatch; ++b)
-      if (!warp_append(P.touched, &P.ks->touched_n, P.n, first[b], w[b]))
+      if (!warp_append(P.touched[S.tsel], &P.ks->touched_n[S.tsel], P.n, first[b], w[b]))
         report_bad(P.sync, 33u, w[b], 0u);
   } else {
 #pragma unroll
@@ -277,29 +278,73 @@ __device__ void peel_phase(const KParams& P, KSmem& S, KCnt& C) {
   }
 }
 
-// Lazy, second phase: each touched vertex takes its count once and moves to its bucket.
+// Lazy, apply phase: every vertex counted in the previous phase takes its count once
+// (priority = max(priority - count, k), read and reset with one atomicExch so that a count
+// arriving concurrently lands either here or in the next list) and moves to its window
+// bucket; a vertex that drops to k is extracted at once -- its out-degrees are scanned
+// across the CTA and its neighbours counted into the other list, as in the peel phase --
+// so one phase per peeling round suffices.  Counts of one level add up: applying them
+// together equals applying them round by round (each decrement is floored at k).
 __device__ void apply_phase(const KParams& P, KSmem& S, KCnt& C) {
-  const uint32_t tn = min(__ldcg(&P.ks->touched_n), P.n);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t r = S.tsel ^ 1u;
+  const uint32_t tn = min(__ldcg(&P.ks->touched_n[r]), P.n);
   const uint32_t k = S.k;
+  const uint32_t* nb = reinterpret_cast<const uint32_t*>(P.adj);
   for (uint32_t i0 = blockIdx.x * kBlock; i0 < tn; i0 += gridDim.x * kBlock) {
-    const uint32_t i = i0 + threadIdx.x;
+    const uint32_t i = i0 + tid;
     bool has = i < tn;
-    uint32_t w = 0, np = 0;
+    uint32_t w = 0, np = 0, beg = 0, deg = 0;
     if (has) {
-      w = __ldcg(P.touched + i);
+      w = __ldcg(P.touched[r] + i);
       if (w < P.n) {
-        const uint32_t c = __ldcg(P.cnt + w);
-        P.cnt[w] = 0u;
-        const uint32_t p = __ldcg(P.prio + w);  // > k: it was counted this round
-        np = p - k > c ? p - c : k;
-        P.prio[w] = np;
-        C.improved++;
+        const uint32_t c = atomicExch(P.cnt + w, 0u);
+        const uint32_t p = __ldcg(P.prio + w);  // > k: it was counted at this level
+        if (p > k) {
+          np = p - k > c ? p - c : k;
+          P.prio[w] = np;
+          C.improved++;
+          if (np == k) {  // dropped to the level: extracted now
+            C.items++;
+            beg = __ldg(P.off + w);
+            deg = __ldg(P.off + w + 1) - beg;
+            if (deg >= P.hub_min && P.hub && push_khub(P, w, beg, beg + deg)) deg = 0;
+          }
+        } else {
+          has = false;
+        }
       } else {
         report_bad(P.sync, 34u, w, i);
         has = false;
       }
     }
-    insert_prio(P, S, C, has, w, np);
+    const bool to_ring = has && np != k && np - S.base < kKRing;
+    C.inserts += to_ring ? 1u : 0u;
+    ring_insert(P, to_ring, np - S.base, w);
+    S.lb_pos[tid] = deg;
+    S.lb_beg[tid] = beg;
+    __syncthreads();
+    kscan(S.lb_pos, S.wtmp);
+    const uint32_t etot = S.lb_pos[kBlock];
+    for (uint32_t e0 = 0; e0 < etot; e0 += kBlock * kKBatch) {
+      bool ok[kKBatch];
+      uint32_t wv[kKBatch];
+#pragma unroll
+      for (int b = 0; b < kKBatch; ++b) {
+        const uint32_t idx = e0 + (uint32_t)b * kBlock + tid;
+        ok[b] = idx < etot;
+        uint32_t j = 0;
+        if (ok[b]) {
+#pragma unroll
+          for (uint32_t s = kBlock / 2; s > 0; s >>= 1)
+            if (S.lb_pos[j + s] <= idx) j += s;
+        }
+        const uint32_t e = S.lb_beg[j] + (idx - S.lb_pos[j]);
+        wv[b] = ok[b] ? __ldg(nb + 2 * (size_t)e) : 0u;
+      }
+      update_batch(P, S, C, ok, wv);
+    }
+    __syncthreads();
   }
 }
 
@@ -365,6 +410,24 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
     }
     return kKPeel;
   };
+  // The level is done: the next non-empty (or overflowed) bucket of the window, else a
+  // refill of the window from the smallest priority above it.
+  auto level_done = [&]() -> uint32_t {
+    const uint32_t cur = __ldcg(&ks->cur);
+    for (uint32_t c0 = cur + 1; c0 < kKRing; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      const bool ne = c < kKRing && (__ldcg(P.counts + c) > 0u || __ldcg(P.lossy + c) != 0u);
+      const unsigned b = __ballot_sync(FULL, ne);
+      if (b) return start_level(c0 + (uint32_t)(__ffs(b) - 1));
+    }
+    if (lane == 0) {  // window exhausted: refill from the smallest priority above it
+      ks->lo = __ldcg(&ks->base) + kKRing;
+      ks->kmin = kInf;
+      ks->refills = __ldcg(&ks->refills) + 1u;
+    }
+    return kKMin;
+  };
+  // Eager: vertices that dropped to k wait in list[asel]; they are the next round.
   auto after_round = [&]() -> uint32_t {
     if (lane == 0) P.stats->v[kStRounds] += 1ull;
     const uint32_t a = __ldcg(&ks->asel);
@@ -379,19 +442,21 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
       }
       return kKPeel;
     }
-    const uint32_t cur = __ldcg(&ks->cur);
-    for (uint32_t c0 = cur + 1; c0 < kKRing; c0 += 32) {
-      const uint32_t c = c0 + lane;
-      const bool ne = c < kKRing && (__ldcg(P.counts + c) > 0u || __ldcg(P.lossy + c) != 0u);
-      const unsigned b = __ballot_sync(FULL, ne);
-      if (b) return start_level(c0 + (uint32_t)(__ffs(b) - 1));
+    return level_done();
+  };
+  // Lazy: the vertices counted into touched[tsel] are applied (and those that drop to k
+  // extracted) by the next apply phase, which counts into the other list, reset here.
+  auto lazy_next = [&]() -> uint32_t {
+    if (lane == 0) P.stats->v[kStRounds] += 1ull;
+    const uint32_t t = __ldcg(&ks->tsel);
+    if (__ldcg(&ks->touched_n[t]) > 0u) {
+      if (lane == 0) {
+        ks->tsel = t ^ 1u;
+        ks->touched_n[t ^ 1u] = 0u;
+      }
+      return kKApply;
     }
-    if (lane == 0) {  // window exhausted: refill from the smallest priority above it
-      ks->lo = __ldcg(&ks->base) + kKRing;
-      ks->kmin = kInf;
-      ks->refills = __ldcg(&ks->refills) + 1u;
-    }
-    return kKMin;
+    return level_done();
   };
   if (!fatal) {
     switch (done) {
@@ -431,24 +496,19 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
         next = kKPeel;
         break;
       case kKPeel:
+      case kKApply:
         if ((__ldcg(&ks->hub_word) >> 32) > 0u) {  // hubs listed: their edges first
           next = kKHub;
           break;
         }
-        if (!P.eager && __ldcg(&ks->touched_n) > 0u) next = kKApply;
-        else next = after_round();
+        next = P.eager ? after_round() : lazy_next();
         break;
       case kKHub:
         if (lane == 0) {
           ks->hub_word = 0ull;
           ks->hub_claim = 0u;
         }
-        if (!P.eager && __ldcg(&ks->touched_n) > 0u) next = kKApply;
-        else next = after_round();
-        break;
-      case kKApply:
-        if (lane == 0) ks->touched_n = 0u;
-        next = after_round();
+        next = P.eager ? after_round() : lazy_next();
         break;
       default:
         next = kKStop;
@@ -505,6 +565,7 @@ __device__ void kbarrier(const KParams& P, KSmem& S, uint32_t& bar, uint32_t don
     S.fsel = __ldcg(&ks->fsel);
     S.fr_n = __ldcg(&ks->fr_n);
     S.asel = __ldcg(&ks->asel);
+    S.tsel = __ldcg(&ks->tsel);
     S.t_bar += gtimer() - t_in;
   }
   __syncthreads();
