@@ -6,7 +6,7 @@ sources and targets); it holds none of the shortest-path arithmetic.  The large 
 small irregular test graphs are built here with numpy.  All draws are seeded.
 
 Workload recipes (the paper's own datasets -- RoadUSA, Germany, Massachusetts, social
-and web graphs, Table "Graphs used for experiments" in Section 6 -- are not available;
+and web graphs, the table of datasets in Section 6 -- are not available;
 these synthetic graphs stand in for them):
 
 * ``grid(256, 256, 1, 1000, seed=1)``: 4-neighbour grid, weights uniform in [1, 1000).

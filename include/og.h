@@ -3,10 +3,9 @@
  *
  * The library computes single-source and point-to-point shortest paths with
  * Delta-stepping over a bucketed priority queue, using eager bucket updates and bucket
- * fusion (Section 3.2, "Eager Bucket Update", and Section 3.3, "Eager Bucket Fusion
- * Optimization", with the figure "SSSP with the eager bucket update approach and the
- * bucket fusion optimization").  Weighted BFS, PPSP and A* are variants of the same
- * loop (Section 6.1, "Applications").  The lazy bucket update (Section 3.1), the
+ * fusion (Section 3.2, the eager bucket update, and Section 3.3, bucket fusion, with
+ * their figure of SSSP with eager updates and fusion).  Weighted BFS, PPSP and A* are
+ * variants of the same loop (Section 6.1).  The lazy bucket update (Section 3.1), the
  * unordered Bellman-Ford baseline and k-core by peeling (Section 6.1, lazy with the
  * constant-sum reduction of Section 5.1, or eager) complete the comparisons of Section
  * 6.4.  Every step runs in CUDA kernels for sm_103a; there is no CPU fallback.
@@ -64,8 +63,8 @@ extern "C" {
 typedef struct og_graph og_graph;
 typedef struct og_server og_server;
 
-/* Schedule knobs: the scheduling language of Section 4.2 (Table "Scheduling functions
- * for applyUpdatePriority operators") as plain fields.  0 selects the graph's tuned or
+/* Schedule knobs: the scheduling language of Section 4.2 (its table of scheduling
+ * functions for priority updates) as plain fields.  0 selects the graph's tuned or
  * default value for every field. */
 typedef struct og_config {
   uint32_t delta;            /* priority coarsening factor (Section 2), >= 1          */

@@ -1341,7 +1341,7 @@ int autotune_queries(og_graph* g, const std::vector<og_query>& qs, uint32_t delt
       }
     }
   }
-  // Fusion threshold (Section 5.2, configBucketFusionThreshold), frontier tile, CTAs/SM.
+  // Fusion threshold (Section 5.2's scheduling function for it), frontier tile, CTAs/SM.
   for (uint32_t f : {OG_FUSION_OFF, 256u, 1024u, 2048u, 0xFFFFFFFFu}) {
     og_config c = best;
     c.fusion_threshold = f;

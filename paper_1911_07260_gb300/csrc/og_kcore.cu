@@ -1,6 +1,6 @@
 // Device side of k-core decomposition by peeling (Section 6.1, "k-core"), with the two
-// bucket-update strategies the paper compares (Section 6.4, table "Performance Impact of
-// Eager and Lazy Bucket Updates"):
+// bucket-update strategies the paper compares (Section 6.4, the table comparing
+// eager and lazy bucket updates):
 //   * lazy with the constant-sum (histogram) reduction of Section 5.1: a round extracts
 //     the frontier (every vertex whose priority equals the level k) and only counts, per
 //     neighbour w with priority above k, how many extracted vertices it lost; a second

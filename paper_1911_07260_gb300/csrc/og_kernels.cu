@@ -1,7 +1,7 @@
 // Device side of libog: Delta-stepping with eager bucket update and bucket fusion.
 //
-// Mapping of the paper's method (Section 3.2 / 3.3, figure "SSSP with the eager bucket
-// update approach and the bucket fusion optimization") onto one persistent,
+// Mapping of the paper's method (Section 3.2 / 3.3 and the figure of SSSP with
+// eager bucket updates and bucket fusion) onto one persistent,
 // cooperatively launched kernel:
 //   * the thread-local buckets of the paper become CTA-local bins in shared memory for
 //     the current bucket, plus per-query materialised global buckets (a ring of B device
@@ -945,7 +945,8 @@ extern "C" __global__ void og_fill_kernel(uint32_t* dist, uint32_t n, const uint
 }
 
 // Starts the listed queries: dist[src] = 0 and the start vertex in its first bucket
-// (Section 3.2 figure: Dist[startV] = 0 and the bucket structure holding startV).
+// (the initial state of the Section 3.2 figures: the source at distance 0, alone in its
+// bucket).
 extern "C" __global__ void og_init_kernel(Params P, const uint32_t* slots, uint32_t nslots) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nslots) return;

@@ -267,8 +267,8 @@ def test_invalid_arguments(og, gg, grid256):
 
 
 def test_fusion_cuts_rounds_on_road_graph(og, orc, road300):
-    """Section 6.4 (Table "Running times and number of rounds reductions with the bucket
-    fusion optimization"): fusion processes the same bucket without a global round;
+    """Section 6.4 (the table of running times and rounds with and without bucket
+    fusion): fusion processes the same bucket without a global round;
     the result is unchanged and the number of global rounds drops."""
     g, G = road300
     ref = orc.dijkstra(g, 0)
