@@ -215,7 +215,7 @@ int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats
  *   cfg: NULL or a config; used fields: expand_tile (frontier entries per claim, rounded
  *        up to 256; a small frontier gets smaller tiles), hub_degree (frontier vertices
  *        of at least this out-degree have their edges split over every warp of the grid;
- *        0 = 256 here), blocks_per_sm, spin_limit_ns,
+ *        0 = 256 here), blocks_per_sm (0 = 2 here), spin_limit_ns,
  *        arena_entries (vertex ids held by the
  *        256 materialised buckets; default 4n; a bucket that runs out of space is rebuilt
  *        by a scan at its level, so any size gives the same result).
