@@ -1,0 +1,60 @@
+"""bench.py's host-side arithmetic (CPU only): the algorithmic-byte model of the roofline,
+the reached-edge count behind GTEPS, the traffic scaling from the small ncu capture, the
+argument parser and the reference arm's metric table."""
+import numpy as np
+
+import bench
+
+
+def test_reached_edges_and_algo_bytes(gg, orc):
+    # a path 0 -> 1 -> 2 plus an unreachable vertex 3 with two out-edges
+    g = gg.from_edges(4, [0, 1, 3, 3], [1, 2, 0, 2], [5, 5, 1, 1])
+    d = orc.dijkstra(g, 0)
+    m_r, n_r = bench.reached_edges(g, d)
+    assert (m_r, n_r) == (2, 3)  # edges out of 0 and 1 (2 has none); 0, 1, 2 reached
+    assert bench.algo_bytes(m_r, n_r, g.n) == 12 * 2 + 28 * 3 + 4 * 4
+
+
+def test_algo_bytes_of_the_road_workload_per_source():
+    # the road-like 4900 x 4900 workload's figure quoted with the roofline: 12 m + 28 n + 4 n
+    # bytes per source when every vertex is reached (the road graph is one component)
+    n, m = 23997150, 82565692
+    per_source = bench.algo_bytes(m, n, n)
+    assert per_source == 12 * m + 32 * n
+    assert per_source * 8 == 14069576832  # the bench's bytes_per_launch for 8 sources
+
+
+def test_scaled_traffic_follows_vertices_times_sources(monkeypatch):
+    cap = dict(bench.TRAFFIC_CAPTURE)
+    monkeypatch.setattr(bench, "kernel_sha", lambda: cap["kernel_sha"])
+    full = bench.scaled_traffic("road", cap["n"] * 4, cap["sources"], 1)
+    assert full == int(cap["bytes"] * 4)
+    half = bench.scaled_traffic("road", cap["n"], cap["sources"] // 2, 1)
+    assert half == int(cap["bytes"] / 2)
+    # another graph kind, the barrier-free engine or a changed kernel: no figure
+    assert bench.scaled_traffic("rmat", cap["n"], cap["sources"], 1) is None
+    assert bench.scaled_traffic("road", cap["n"], cap["sources"], 2) is None
+    monkeypatch.setattr(bench, "kernel_sha", lambda: "0" * 16)
+    assert bench.scaled_traffic("road", cap["n"], cap["sources"], 1) is None
+
+
+def test_kernel_sha_covers_the_kernel_sources():
+    sha = bench.kernel_sha()
+    assert len(sha) == 16 and int(sha, 16) >= 0
+    assert any(f.endswith("og_kernels.cu") for f in bench.KERNEL_SOURCES)
+
+
+def test_parser_defaults_and_workloads():
+    a = bench.parse_args([])
+    assert (a.gpus, a.workload, a.warmup) == (1, "road-sssp", 3) and a.warmup >= 3
+    assert a.impl == "ours" and a.side == 4900 and a.sources == 8
+    for w in ("rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf", "road-lazy",
+              "rmat-lazy", "rmat-kcore"):
+        assert bench.parse_args(["--workload", w]).workload == w
+
+
+def test_reference_metrics_name_every_workload():
+    choices = {"road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf",
+               "road-lazy", "rmat-lazy", "rmat-kcore"}
+    assert set(bench.REF_METRIC) == choices
+    assert "queries/s" in bench.REF_METRIC["batch"] and "GTEPS" in bench.REF_METRIC["road-sssp"]
