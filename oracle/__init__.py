@@ -3,7 +3,8 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this package.  It computes the plain definition of shortest-path distances
 (``oracle.c``: Dijkstra, BFS, Bellman-Ford, certificate check) and
-k-core coreness by peeling and shares no code with
+k-core coreness by peeling, approximate set cover by bucketed nearly independent
+steps, and shares no code with
 the CUDA path in ``paper_1911_07260_gb300``.
 
 Each wrapper takes a ``graphgen.Graph`` (CSR: uint64 offsets, uint32 neighbours,
@@ -56,6 +57,8 @@ def _load():
         L.or_check_sssp.argtypes = [u32, vp, vp, vp, u32, vp, vp]
         L.or_kcore.restype = ctypes.c_int
         L.or_kcore.argtypes = [u32, vp, vp, vp]
+        L.or_setcover.restype = ctypes.c_int
+        L.or_setcover.argtypes = [u32, vp, vp, u32, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -130,3 +133,18 @@ def kcore(g) -> np.ndarray:
     out = np.empty(g.n, np.uint32)
     _status(_load().or_kcore(g.n, off.ctypes.data, nbr.ctypes.data, out.ctypes.data), False)
     return out
+
+
+def setcover(g, pri, eps_ppm: int = 10000) -> tuple[np.ndarray, int]:
+    """Approximate unweighted set cover of the sets S_v = adjacency of v (``oracle.c``,
+    ``or_setcover``).  ``pri`` is a permutation of 0..n-1 (the sets' priorities).
+    Returns (step at which each set joined the cover, 0 = never; number of steps)."""
+    off, nbr, _ = _csr(g)
+    p = np.ascontiguousarray(pri, dtype=np.uint32)
+    if p.shape != (g.n,):
+        raise OracleError("priorities must have one entry per vertex")
+    out = np.empty(g.n, np.uint32)
+    steps = ctypes.c_uint64(0)
+    _status(_load().or_setcover(g.n, off.ctypes.data, nbr.ctypes.data, int(eps_ppm),
+                                p.ctypes.data, out.ctypes.data, ctypes.byref(steps)), False)
+    return out, int(steps.value)

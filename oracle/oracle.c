@@ -1,5 +1,5 @@
 /*
- * CPU oracle for shortest-path distances -- TEST INFRASTRUCTURE ONLY.
+ * CPU oracle for shortest-path distances, k-core and set cover -- TEST INFRASTRUCTURE ONLY.
  *
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load this
  * library.  The product path (paper_1911_07260_gb300) never calls it and shares no
@@ -31,6 +31,27 @@
  *                       entries, so on a symmetric simple graph this is the usual
  *                       coreness; the minimum is taken with the binary heap above
  *                       (stale heap entries are skipped).
+ *   - or_setcover:      approximate unweighted set cover (Section 6.1, "Approximate Set
+ *                       Cover"), the graph read as a set system: the set of vertex v is
+ *                       its adjacency list S_v (entries counted with multiplicity), the
+ *                       universe is the union of the S_v, every set costs 1.  Sets are
+ *                       bucketed by the number of their still uncovered elements on the
+ *                       integer ladder t_0 = 1, t_(j+1) = t_j + max(1, floor(t_j * eps)),
+ *                       eps = eps_ppm / 10^6 (bucket j: t_j <= D < t_(j+1)).  The highest
+ *                       non-empty bucket j is worked off in steps; one step (1) recounts
+ *                       D for each set of the bucket: D = 0 leaves, 0 < D < t_j moves to
+ *                       the bucket of D, the rest are active; (2) gives each uncovered
+ *                       element of an active set to the active set of smallest priority
+ *                       that contains it; (3) lets every active set that received at
+ *                       least tau_j = ceil(t_j / (1 + eps)) of its elements join the cover
+ *                       (a nearly independent subset of the bucket) and cover all of its
+ *                       elements; the other active sets stay in bucket j.  step_out[v] is
+ *                       the 1-based step in which v joined, 0 if it never did.
+ *                       Parity pinned by closed forms (star, clique), hand-worked paths,
+ *                       invariance under relabelling and disjoint union, and per-step
+ *                       certificates of the approximate greedy choice, the near
+ *                       independence and the (1 + eps)^2 H(max |S|) approximation bound
+ *                       against brute-force optima.
  *
  * Conventions.  Distances are uint32 with 0xFFFFFFFF = unreachable (the paper's INT_MAX
  * initialisation, Section 4.1).  A finite distance >= 0xFFFFFFFE cannot be represented;
@@ -246,5 +267,134 @@ int or_kcore(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t *cor
   free(prio);
   free(done);
   free(h);
+  return OR_OK;
+}
+
+/* Bucket of a residual size d >= 1 on the ladder t[0 .. nb] (t[nb] > every size):
+ * the largest j with t[j] <= d. */
+static uint32_t sc_bucket(const uint64_t *t, uint32_t nb, uint64_t d) {
+  uint32_t lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (t[mid] <= d) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+int or_setcover(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t eps_ppm,
+                const uint32_t *pri, uint32_t *step_out, uint64_t *steps_out) {
+  if (n == 0 || eps_ppm > 1000000u) return OR_INVALID;
+  const uint64_t M = 1000000ull;
+  /* priorities: a permutation of 0 .. n-1 */
+  unsigned char *seen = (unsigned char *)calloc(n, 1);
+  if (!seen) return OR_NOMEM;
+  for (uint32_t v = 0; v < n; ++v) {
+    if (pri[v] >= n || seen[pri[v]]) {
+      free(seen);
+      return OR_INVALID;
+    }
+    seen[pri[v]] = 1;
+  }
+  free(seen);
+  uint64_t maxdeg = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    step_out[v] = 0;
+    if (off[v + 1] - off[v] > maxdeg) maxdeg = off[v + 1] - off[v];
+  }
+  *steps_out = 0;
+  if (maxdeg == 0) return OR_OK;
+  /* the ladder, until it passes the largest set */
+  uint64_t tcap = 64, nb = 0;
+  uint64_t *t = (uint64_t *)malloc(sizeof(uint64_t) * tcap);
+  if (!t) return OR_NOMEM;
+  t[0] = 1;
+  while (t[nb] <= maxdeg) {
+    uint64_t step = t[nb] * eps_ppm / M;
+    if (step < 1) step = 1;
+    if (nb + 2 > tcap) {
+      tcap *= 2;
+      uint64_t *t2 = (uint64_t *)realloc(t, sizeof(uint64_t) * tcap);
+      if (!t2) {
+        free(t);
+        return OR_NOMEM;
+      }
+      t = t2;
+    }
+    t[nb + 1] = t[nb] + step;
+    ++nb;
+  }
+  /* bucket lists as singly linked lists (a set is in one list at a time) */
+  uint32_t *head = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+  uint32_t *nxt = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  uint32_t *mem = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  uint32_t *act = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  uint32_t *join = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  uint32_t *claim = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  unsigned char *cov = (unsigned char *)calloc(n, 1);
+  if (!head || !nxt || !mem || !act || !join || !claim || !cov) {
+    free(t); free(head); free(nxt); free(mem); free(act); free(join); free(claim); free(cov);
+    return OR_NOMEM;
+  }
+  for (uint64_t j = 0; j < nb; ++j) head[j] = UNREACHED;
+  for (uint32_t v = n; v-- > 0;) {
+    uint64_t d = off[v + 1] - off[v];
+    if (d == 0) continue;
+    uint32_t j = sc_bucket(t, (uint32_t)nb, d);
+    nxt[v] = head[j];
+    head[j] = v;
+  }
+  uint64_t step = 0;
+  for (uint32_t j = (uint32_t)nb; j-- > 0;) {
+    uint32_t cnt = 0;
+    for (uint32_t v = head[j]; v != UNREACHED; v = nxt[v]) mem[cnt++] = v;
+    head[j] = UNREACHED;
+    const uint64_t tau = (t[j] * M + (M + eps_ppm) - 1) / (M + eps_ppm);
+    while (cnt > 0) {
+      ++step;
+      /* (1) recount the uncovered elements of each set of the bucket */
+      uint32_t na = 0;
+      for (uint32_t i = 0; i < cnt; ++i) {
+        uint32_t v = mem[i];
+        uint64_t d = 0;
+        for (uint64_t e = off[v]; e < off[v + 1]; ++e) d += cov[nbr[e]] ? 0 : 1;
+        if (d == 0) continue;
+        if (d < t[j]) {
+          uint32_t jb = sc_bucket(t, (uint32_t)nb, d);
+          nxt[v] = head[jb];
+          head[jb] = v;
+          continue;
+        }
+        act[na++] = v;
+      }
+      /* (2) each uncovered element goes to the smallest-priority active set holding it */
+      for (uint32_t i = 0; i < na; ++i)
+        for (uint64_t e = off[act[i]]; e < off[act[i] + 1]; ++e)
+          if (!cov[nbr[e]]) claim[nbr[e]] = UNREACHED;
+      for (uint32_t i = 0; i < na; ++i)
+        for (uint64_t e = off[act[i]]; e < off[act[i] + 1]; ++e) {
+          uint32_t u = nbr[e];
+          if (!cov[u] && pri[act[i]] < claim[u]) claim[u] = pri[act[i]];
+        }
+      /* (3) sets that received at least tau of their elements join; the rest stay */
+      uint32_t nj = 0, nl = 0;
+      for (uint32_t i = 0; i < na; ++i) {
+        uint32_t v = act[i];
+        uint64_t won = 0;
+        for (uint64_t e = off[v]; e < off[v + 1]; ++e)
+          won += (!cov[nbr[e]] && claim[nbr[e]] == pri[v]) ? 1 : 0;
+        if (won >= tau) join[nj++] = v;
+        else mem[nl++] = v;
+      }
+      for (uint32_t i = 0; i < nj; ++i) {
+        uint32_t v = join[i];
+        step_out[v] = (uint32_t)step;
+        for (uint64_t e = off[v]; e < off[v + 1]; ++e) cov[nbr[e]] = 1;
+      }
+      cnt = nl;
+    }
+  }
+  *steps_out = step;
+  free(t); free(head); free(nxt); free(mem); free(act); free(join); free(claim); free(cov);
   return OR_OK;
 }
