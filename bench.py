@@ -21,7 +21,8 @@ road-bf (the default graph and sources by the unordered Bellman-Ford baseline, w
 ordered method's time on the same sources for the comparison of Section 6), rmat-kcore
 (coreness of R-MAT scale 24 by peeling, lazy with the histogram reduction and eager),
 road-lazy / rmat-lazy (SSSP with the lazy bucket update, the eager update's time on the
-same sources beside it: the eager-vs-lazy comparison of Section 6.4).
+same sources beside it: the eager-vs-lazy comparison of Section 6.4), rmat-setcover
+(approximate set cover of R-MAT scale 24, eps = 0.01, seeded random priorities).
 
 --impl reference times the CPU oracle (single-threaded Dijkstra) on the same workload
 and metric, one bounded sample per step.
@@ -56,7 +57,7 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="road-sssp",
                    choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf",
-                            "rmat-kcore", "road-lazy", "rmat-lazy"])
+                            "rmat-kcore", "road-lazy", "rmat-lazy", "rmat-setcover"])
     p.add_argument("--side", type=int, default=4900, help="road-like grid side")
     p.add_argument("--scale", type=int, default=24, help="R-MAT scale")
     p.add_argument("--sources", type=int, default=8)
@@ -437,13 +438,15 @@ REF_METRIC = {
     "batch": "batched queries/s (128 SSSP + 128 PPSP per launch)",
     "serve": "served A*/PPSP queries/s with p50/p99 latency",
     "rmat-kcore": "k-core GTEPS (directed edges / time, lazy bucket update with histogram)",
+    "rmat-setcover": "set cover GTEPS (directed edges / time, eps = 0.01)",
 }
 
 
 def run_reference(args):
     """The CPU oracle as it stands, on the same workload, metric and unit as our arm: one
     bounded sample per step (a full Dijkstra for the SSSP family, one query of the batch
-    or of the served stream, or a k-core peeling of R-MAT scale 20 for rmat-kcore)."""
+    or of the served stream, a k-core peeling of R-MAT scale 20 for rmat-kcore, one set
+    cover of R-MAT scale 20 for rmat-setcover)."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
@@ -451,7 +454,17 @@ def run_reference(args):
     import oracle
     wl = args.workload
     samples = []  # (units, seconds) per timed step
-    if wl == "rmat-kcore":
+    if wl == "rmat-setcover":
+        g = graphgen.rmat(20, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
+        pri = graphgen.priorities(g.n, seed=1)
+        gname, unit = "R-MAT scale 20 (sample of the scale-24 workload)", "GTEPS"
+        what = "one approximate set cover (eps = 0.01) of R-MAT scale 20 per step"
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.setcover(g, pri, 10000)
+            if i >= args.warmup:
+                samples.append((g.m, time.perf_counter() - t0))
+    elif wl == "rmat-kcore":
         g = graphgen.rmat(20, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
         gname, unit = "R-MAT scale 20 (sample of the scale-24 workload)", "GTEPS"
         what = "one k-core peeling (binary heap) of R-MAT scale 20 per step"
@@ -828,6 +841,108 @@ def run_kcore(args):
     print(json.dumps(line), flush=True)
 
 
+def run_setcover(args):
+    """Approximate set cover of the R-MAT scale-24 graph (Section 6.1): sets = adjacency
+    lists, eps = 0.01, seeded random priorities; one persistent launch per step (plus the
+    set-up kernels).  GTEPS = directed edges / device time per step."""
+    import torch
+    import graphgen
+    import oracle
+    import paper_1911_07260_gb300 as og
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    eps = 10000
+    g = graphgen.rmat(args.scale, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
+    G = og.Graph.from_csr(g)
+    cfg = og.config(hub_degree=args.hub) if args.hub else None
+    pri = graphgen.priorities(g.n, seed=1)
+    dpri = torch.from_numpy(pri.view(np.int32)).cuda()
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    _, st0 = og.setcover(G, eps, dpri, cfg=cfg, out=out)
+    ref = out.cpu().numpy().view(np.uint32).copy()
+    for _ in range(args.warmup):
+        og.setcover(G, eps, dpri, cfg=cfg, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernel_ns = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, st = og.setcover(G, eps, dpri, cfg=cfg, out=out)
+            kernel_ns += st.kernel_ns
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    kernel_s = kernel_ns / 1e9 / args.steps
+    clocks = clk.summary()
+    same = bool(np.array_equal(out.cpu().numpy().view(np.uint32), ref))
+    # end to end through the public call with host buffers: priorities in, steps out
+    host = np.empty(g.n, np.uint32)
+    reps = max(2, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        og.setcover(G, eps, pri, cfg=cfg, out=host)
+    e2e_s = (time.perf_counter() - t0) / reps
+    same &= bool(np.array_equal(host, ref))
+    # algorithmic bytes of one pass over the set system: per adjacency entry the element
+    # id (4), its covered flag (1), one claim and one claim check (8 + 8); per vertex its
+    # offsets (8) and its result (4)
+    bytes_step = 21 * g.m + 12 * g.n
+    peak, peak_kind = peaks()
+    cpu = None
+    exact = None
+    if not args.no_cpu_baseline:
+        # the whole workload is a bounded sample here (about 25 s on one core), and the
+        # method is deterministic: the oracle's cover must equal ours set for set
+        t0 = time.perf_counter()
+        oref, osteps = oracle.setcover(g, pri, eps)
+        dt = time.perf_counter() - t0
+        exact = bool(np.array_equal(oref, ref)) and osteps == int(st0.rounds)
+        cpu = {"value": round(g.m / dt / 1e9, 5), "unit": "GTEPS", "cores": 1,
+               "kind": "oracle",
+               "sample": f"the oracle's set cover of the whole workload ({g.n} V, {g.m} E), "
+                         f"{dt:.1f} s"}
+    chosen = int((ref > 0).sum())
+    line = {
+        "metric": REF_METRIC["rmat-setcover"],
+        "value": round(g.m / step_s / 1e9, 4), "unit": "GTEPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"R-MAT scale {args.scale} approximate set cover (sets = "
+                               "adjacency lists, eps = 0.01, random priorities), one "
+                               "persistent launch per step", "n": g.n, "m": g.m,
+                   "hub_degree": args.hub or 32,
+                   "l2": "inputs larger than L2 (graph %.0f MB)" % (8 * g.m / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round(bytes_step / kernel_s / 1e9 / peak, 4), "traffic": None,
+                     "peak_source": peak_kind, "kernel": "og_setcover_kernel",
+                     "bytes_per_launch": bytes_step, "kernel_ms": round(kernel_s * 1e3, 3)},
+        "setcover": {"sets_chosen": chosen, "steps": int(st.rounds),
+                     "buckets": int(st.fused_iters), "set_visits": int(st.items),
+                     "elements_scanned": int(st.relax), "moves": int(st.global_inserts),
+                     "cta_time_share": {
+                         k: round(v / max(1, st.t_frontier_ns + st.t_fused_ns + st.t_hub_ns
+                                          + st.t_barrier_ns), 3)
+                         for k, v in (("pack_claim", st.t_frontier_ns),
+                                      ("count_join", st.t_fused_ns),
+                                      ("gather", st.t_hub_ns), ("barrier", st.t_barrier_ns))}},
+        "repeat_and_host_output_identical": same,
+        "exact_vs_oracle_full_size": exact,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(g.m / e2e_s / 1e9, 4), "unit": "GTEPS",
+                "h2d_bytes_per_step": 4 * g.n, "d2h_bytes_per_step": 4 * g.n,
+                "ms_per_step": round(e2e_s * 1e3, 3)},
+        "gpu_launches": 5 * args.steps,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -837,6 +952,8 @@ def main(argv=None):
         run_batch(args)
     elif args.workload == "rmat-kcore":
         run_kcore(args)
+    elif args.workload == "rmat-setcover":
+        run_setcover(args)
     elif args.workload == "serve":
         run_serve(args)
     else:

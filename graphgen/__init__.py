@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
 
 This module only lays out graphs and queries (vertices, edges, weights, coordinates,
-sources and targets); it holds none of the shortest-path arithmetic.  The large families
+sources and targets, set priorities); it holds none of the shortest-path, k-core or
+set cover arithmetic.  The large families
 (grid, road-like grid, R-MAT) are built by ``graphgen.cpp`` (compiled by :func:`build`);
 small irregular test graphs are built here with numpy.  All draws are seeded.
 
@@ -199,6 +200,12 @@ def sample_sources(g: Graph, count: int, seed: int = 2) -> np.ndarray:
     if cand.size == 0:
         raise ValueError("graph has no vertex with an out-edge")
     return cand[rng.choice(cand.size, size=count, replace=cand.size < count)].astype(np.uint32)
+
+
+def priorities(n: int, seed: int = 3) -> np.ndarray:
+    """A seeded uniformly random permutation of 0..n-1 (the set priorities of approximate
+    set cover, drawn once and passed to both the oracle and the CUDA path)."""
+    return np.random.default_rng(seed).permutation(n).astype(np.uint32)
 
 
 def sample_pairs_grid_steps(g: Graph, count: int, kmin: int, kmax: int, seed: int = 2,

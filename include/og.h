@@ -8,7 +8,8 @@
  * variants of the same loop (Section 6.1).  The lazy bucket update (Section 3.1), the
  * unordered Bellman-Ford baseline and k-core by peeling (Section 6.1, lazy with the
  * constant-sum reduction of Section 5.1, or eager) complete the comparisons of Section
- * 6.4.  Every step runs in CUDA kernels for sm_103a; there is no CPU fallback.
+ * 6.4; approximate set cover (Section 6.1) is the other bucketed ordered algorithm of
+ * the paper's evaluation.  Every step runs in CUDA kernels for sm_103a; there is no CPU fallback.
  *
  * Conventions shared by every entry point
  *   - Vertices are uint32 ids in [0, n).  Weights are non-negative uint32.
@@ -231,6 +232,39 @@ int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats
 #define OG_KCORE_EAGER 1u
 int og_kcore(og_graph* g, uint32_t mode, const og_config* cfg, uint32_t* core_out,
              og_stats* stats, void* stream);
+
+/* og_setcover: approximate unweighted set cover (Section 6.1, "Approximate Set Cover") of
+ * the graph's set system: the set of vertex v is its out-adjacency list S_v (entries
+ * counted with multiplicity), the universe is the union of all S_v, every set costs 1.
+ * Sets are bucketed by their number D of uncovered elements on the integer ladder
+ * t_0 = 1, t_(j+1) = t_j + max(1, floor(t_j * eps_ppm / 10^6)) (bucket j: t_j <= D <
+ * t_(j+1)), and the highest non-empty bucket j is worked off in steps.  One step
+ * (1) recounts D for every set of bucket j: D = 0 leaves, D < t_j moves to the bucket of
+ * D, the others are active; (2) gives every uncovered element of an active set to the
+ * active set of smallest priority that contains it; (3) adds to the cover every active
+ * set that received at least ceil(t_j * 10^6 / (10^6 + eps_ppm)) elements -- a nearly
+ * independent subset of the bucket -- and marks all of its elements covered; the others
+ * stay in bucket j.  The result depends only on the graph, eps_ppm and the priorities.
+ * Each chosen set covers at least (largest residual) / (1 + eps)^2 new elements, so the
+ * cover is within (1 + eps)^2 H(largest set) of the optimum.
+ *   eps_ppm: eps in millionths, 0 .. 1000000 (10000 = 0.01).
+ *   priority: uint32[n], host or device, a permutation of 0 .. n-1 (random priorities
+ *        give the method's expected number of steps per bucket); NULL = the identity.
+ *   cfg: NULL or a config; used fields: hub_degree (a set with at least this many
+ *        uncovered elements has them split over every warp of the grid; 0 = 32; clamped
+ *        to [16, 2^26]), blocks_per_sm (0 = 2), spin_limit_ns.
+ *   step_out: uint32[n], host or device: the 1-based step in which set v joined the
+ *        cover, 0 if it did not.
+ *   stats (may be NULL): rounds = steps, fused_iters = buckets worked off, items = set
+ *        visits, relax = elements scanned, improved = sets chosen, global_inserts = sets
+ *        moved to a lower bucket, kernel_ns (including the set-up kernels), and summed
+ *        over CTAs: t_frontier_ns (pack and claim phases), t_fused_ns (count, join and
+ *        cover phases), t_hub_ns (bucket gathers), t_barrier_ns.
+ * Requirements: every out-degree below 2^30, m below 2^32, at most 2^22 buckets.
+ * Returns OG_E_INVALID for eps_ppm > 10^6, priorities that are not a permutation, a
+ * graph beyond the requirements or a NULL output. */
+int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const og_config* cfg,
+                uint32_t* step_out, og_stats* stats, void* stream);
 
 /* og_ppsp: point-to-point distance (Section 6.1, "PPSP"): Delta-stepping from src that
  * stops on entering bucket i with i * Delta >= the best dist(src, dst) found.

@@ -92,6 +92,7 @@ def lib():
             "og_sssp_delta": (i32, [vp, u32, u32, vp, vp]),
             "og_sssp_bellman_ford": (i32, [vp, u32, vp, P(Stats), vp]),
             "og_kcore": (i32, [vp, u32, P(Config), vp, P(Stats), vp]),
+            "og_setcover": (i32, [vp, u32, vp, P(Config), vp, P(Stats), vp]),
             "og_wbfs": (i32, [vp, u32, vp, vp]),
             "og_ppsp": (i32, [vp, u32, u32, u32, P(u32), vp]),
             "og_astar": (i32, [vp, u32, u32, vp, u32, P(u32), vp]),
@@ -264,6 +265,19 @@ def kcore(g: Graph, mode: int = KCORE_LAZY, cfg=None, out=None, stream=None):
     st = Stats()
     _check(lib().og_kcore(g.handle, mode, ctypes.byref(cfg) if cfg else None, _ptr(out),
                           ctypes.byref(st), _stream(stream)), "og_kcore")
+    return out, st
+
+
+def setcover(g: Graph, eps_ppm: int = 10000, priority=None, cfg=None, out=None, stream=None):
+    """Approximate set cover of the sets S_v = adjacency of v; ``priority`` is a
+    permutation of 0..n-1 (uint32, host array or device tensor; None = identity).
+    Returns (``out`` uint32[n]: step in which each set joined, 0 = never; Stats)."""
+    out = _alloc_dist(g, out)
+    if isinstance(priority, np.ndarray):
+        priority = np.ascontiguousarray(priority, dtype=np.uint32)
+    st = Stats()
+    _check(lib().og_setcover(g.handle, eps_ppm, _ptr(priority), ctypes.byref(cfg) if cfg else None,
+                             _ptr(out), ctypes.byref(st), _stream(stream)), "og_setcover")
     return out, st
 
 

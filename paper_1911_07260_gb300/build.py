@@ -15,9 +15,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libog.so")
-SOURCES = ["og_kernels.cu", "og_async.cu", "og_kcore.cu", "og_api.cu"]
+SOURCES = ["og_kernels.cu", "og_async.cu", "og_kcore.cu", "og_setcover.cu", "og_api.cu"]
 HEADERS = [os.path.join(CSRC, "og_internal.cuh"), os.path.join(CSRC, "og_device.cuh"),
            os.path.join(CSRC, "og_kcore.cuh"),
+           os.path.join(CSRC, "og_setcover.cuh"),
            os.path.join(INCLUDE, "og.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

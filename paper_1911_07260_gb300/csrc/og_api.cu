@@ -18,6 +18,7 @@
 #include "og.h"
 #include "og_internal.cuh"
 #include "og_kcore.cuh"
+#include "og_setcover.cuh"
 
 namespace og {
 cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st);
@@ -38,6 +39,9 @@ cudaError_t kcore_occupancy(int* blocks_per_sm);
 cudaError_t launch_kcore(const KParams& P, int grid, cudaStream_t st);
 cudaError_t launch_kcore_init(const uint32_t* off, uint32_t* prio, uint32_t n, int sms,
                               cudaStream_t st);
+cudaError_t setcover_occupancy(int* blocks_per_sm);
+cudaError_t launch_setcover(const ScParams& P, int grid, cudaStream_t st);
+cudaError_t launch_setcover_prep(const ScParams& P, uint32_t* iota, int sms, cudaStream_t st);
 }  // namespace og
 
 using namespace og;
@@ -114,6 +118,8 @@ struct Workspace {
   DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big, bmap;
   DBuf kprio, kcnt, ktouched, klist, kring, kcounts, klossy, kstate;  // k-core
   DBuf lzbits, lzlist;  // lazy bucket update
+  DBuf sclad, sclen, scpk, sccov, scclaim, scseen, scmeta, scbase, scbl, scsm, sclg, scstate,
+      scpri, scout;  // set cover
   HBuf h_qd, h_qs, h_sync, h_stats, h_slots, h_aq, h_kstate;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // Barrier-free engine: ring positions must read "free" (all ones) before use.  Entries
@@ -124,7 +130,8 @@ struct Workspace {
   void release() {
     for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
                     &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
-                    &kstate, &lzbits, &lzlist})
+                    &kstate, &lzbits, &lzlist, &sclad, &sclen, &scpk, &sccov, &scclaim, &scseen,
+                    &scmeta, &scbase, &scbl, &scsm, &sclg, &scstate, &scpri, &scout})
       b->release();
     for (HBuf* b : {&h_qd, &h_qs, &h_sync, &h_stats, &h_slots, &h_aq, &h_kstate}) b->release();
     clean_upto = 0;
@@ -173,6 +180,8 @@ constexpr uint32_t kDefaultHub = 4096;      // out-degree from which a vertex is
 constexpr uint32_t kHubSlots = 65536;       // hubs listed per round
 constexpr uint32_t kHubChunks = 1u << 20;   // 1024-edge hub chunks per round
 constexpr uint32_t kKcoreHub = 256;         // k-core: default hub out-degree
+constexpr uint32_t kSetcoverHub = 32;       // set cover: residual size of a large set
+constexpr int kSetcoverBps = 2;             // set cover: default CTAs per SM
 constexpr int kKcoreBps = 2;                // k-core: default CTAs per SM
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 
@@ -1039,6 +1048,154 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   acc.v[kStFlush] = hk->scans;
   export_stats(acc, 0, stats);
   if (hy->err & kErrBounds) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
+             hy->bad_code, hy->bad_val, hy->bad_aux);
+    return OG_E_INTERNAL;
+  }
+  if (hy->err & kErrTimeout) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "grid barrier wait gave up");
+    return OG_E_TIMEOUT;
+  }
+  return OG_OK;
+}
+
+int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const og_config* ucfg,
+                uint32_t* step_out, og_stats* stats, void* stream) {
+  if (!g || !step_out || eps_ppm > 1000000u) return OG_E_INVALID;
+  if (g->max_deg > kScLenMask || g->m >= (1ull << 32)) return OG_E_INVALID;
+  const og_config c = resolve(g, ucfg);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& ws = g->ws;
+  const uint32_t n = g->n;
+  const uint64_t m = g->m;
+  if (!g->sms) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int occ = 0;
+  CK(setcover_occupancy(&occ));
+  if (occ < 1) return OG_E_CUDA;
+  const int want = (ucfg && ucfg->blocks_per_sm) ? (int)ucfg->blocks_per_sm : kSetcoverBps;
+  const int bps = std::max(1, std::min(want, occ));
+  // The bucket ladder t_0 = 1, t_(j+1) = t_j + max(1, floor(t_j * eps)) until it passes
+  // the largest set, and the received count a set of bucket j needs to join,
+  // ceil(t_j / (1 + eps)), both in integers.
+  std::vector<uint32_t> lad(1, 1u);
+  while (lad.back() <= g->max_deg) {
+    const uint64_t t = lad.back();
+    const uint64_t inc = std::max<uint64_t>(1, t * eps_ppm / 1000000ull);
+    lad.push_back((uint32_t)(t + inc));
+    if (lad.size() > (size_t)kScMaxBuckets + 1) return OG_E_INVALID;
+  }
+  const uint32_t nb = (uint32_t)lad.size() - 1u;
+  for (uint32_t j = 0; j < nb; ++j)
+    lad.push_back((uint32_t)(((uint64_t)lad[j] * 1000000ull + 1000000ull + eps_ppm - 1) /
+                             (1000000ull + eps_ppm)));
+  const uint32_t nbands = (nb + kScBand - 1) / kScBand;
+  uint32_t hub = (ucfg && ucfg->hub_degree) ? ucfg->hub_degree : kSetcoverHub;
+  hub = std::min(std::max(hub, kScMinHub), kScMaxHub);
+  const uint32_t lg_cap = (uint32_t)std::min<uint64_t>(n, m / hub + 1);
+  // band lists: each set enters each band at most once, sum (first band + 1) <= n + m/16
+  const uint64_t bl_entries = 2ull * ((uint64_t)n + m / kScBand + nbands + 1);
+  const bool dev_out = is_device_ptr(step_out);
+  const bool dev_pri = priority && is_device_ptr(priority);
+  TRY(ws.sclad.ensure(sizeof(uint32_t) * lad.size()));
+  TRY(ws.sclen.ensure(sizeof(uint32_t) * (size_t)n));
+  TRY(ws.scpk.ensure(2 * sizeof(uint32_t) * (size_t)std::max<uint64_t>(m, 1)));
+  TRY(ws.sccov.ensure((size_t)n));
+  TRY(ws.scclaim.ensure(sizeof(unsigned long long) * (size_t)n));
+  TRY(ws.scseen.ensure(sizeof(uint32_t) * (size_t)((n + 31) / 32)));
+  TRY(ws.scmeta.ensure(5 * sizeof(uint32_t) * (size_t)std::max(nbands, 1u)));
+  TRY(ws.scbase.ensure(sizeof(unsigned long long) * (size_t)std::max(nbands, 1u)));
+  TRY(ws.scbl.ensure(sizeof(unsigned long long) * (size_t)bl_entries));
+  TRY(ws.scsm.ensure(8 * sizeof(uint32_t) * (size_t)n));
+  TRY(ws.sclg.ensure(10 * sizeof(uint32_t) * (size_t)lg_cap));
+  TRY(ws.scstate.ensure(sizeof(ScState)));
+  if (!dev_pri) TRY(ws.scpri.ensure(sizeof(uint32_t) * (size_t)n));
+  if (!dev_out) TRY(ws.scout.ensure(sizeof(uint32_t) * (size_t)n));
+  TRY(ws.sync.ensure(sizeof(Sync)));
+  TRY(ws.stats.ensure(sizeof(Stats)));
+  TRY(ws.h_sync.ensure(sizeof(Sync)));
+  TRY(ws.h_stats.ensure(sizeof(Stats)));
+  TRY(ws.h_kstate.ensure(sizeof(ScState)));
+  TRY(ws.events());
+  ScParams P{};
+  P.off = g->off;
+  P.adj = g->adj;
+  P.n = n;
+  P.pri = dev_pri ? priority : ws.scpri.as<uint32_t>();
+  P.step_out = dev_out ? step_out : ws.scout.as<uint32_t>();
+  P.len = ws.sclen.as<uint32_t>();
+  P.pk[0] = ws.scpk.as<uint32_t>();
+  P.pk[1] = P.pk[0] + std::max<uint64_t>(m, 1);
+  P.cov = ws.sccov.as<uint8_t>();
+  P.claim = ws.scclaim.as<unsigned long long>();
+  P.t = ws.sclad.as<uint32_t>();
+  P.tau = P.t + nb + 1;
+  P.nb = nb;
+  P.nbands = nbands;
+  P.bl = ws.scbl.as<unsigned long long>();
+  uint32_t* meta = ws.scmeta.as<uint32_t>();
+  const uint32_t nbm = std::max(nbands, 1u);
+  P.hist = meta;
+  P.bcap = meta + nbm;
+  P.bcnt = meta + 2 * nbm;
+  P.bsel = meta + 3 * nbm;
+  P.bmax = meta + 4 * nbm;
+  P.bbase = ws.scbase.as<unsigned long long>();
+  P.bl_entries = bl_entries;
+  P.seen = ws.scseen.as<uint32_t>();
+  uint32_t* sm = ws.scsm.as<uint32_t>();
+  uint32_t* lg = ws.sclg.as<uint32_t>();
+  for (int q = 0; q < 2; ++q) {
+    uint32_t* a = sm + (size_t)q * 4 * n;
+    P.sm[q] = ScList{a, a + n, a + 2 * (size_t)n, a + 3 * (size_t)n, nullptr};
+    uint32_t* b = lg + (size_t)q * 5 * lg_cap;
+    P.lg[q] = ScList{b, b + lg_cap, b + 2 * (size_t)lg_cap, b + 3 * (size_t)lg_cap,
+                     b + 4 * (size_t)lg_cap};
+  }
+  P.lg_cap = lg_cap;
+  P.hub = hub;
+  P.sync = ws.sync.as<Sync>();
+  P.ss = ws.scstate.as<ScState>();
+  P.stats = ws.stats.as<Stats>();
+  P.spin_ns = c.spin_limit_ns;
+  CK(cudaMemcpyAsync(ws.sclad.p, lad.data(), sizeof(uint32_t) * lad.size(),
+                     cudaMemcpyHostToDevice, st));
+  if (priority && !dev_pri)
+    CK(cudaMemcpyAsync(ws.scpri.p, priority, sizeof(uint32_t) * (size_t)n,
+                       cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(meta, 0, 5 * sizeof(uint32_t) * (size_t)nbm, st));
+  CK(cudaMemsetAsync(P.seen, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), st));
+  CK(cudaMemsetAsync(P.ss, 0, sizeof(ScState), st));
+  CK(cudaMemsetAsync(P.sync, 0, sizeof(Sync), st));
+  CK(cudaMemsetAsync(P.stats, 0, sizeof(Stats), st));
+  CK(cudaEventRecord(ws.e0, st));
+  CK(launch_setcover_prep(P, priority ? nullptr : ws.scpri.as<uint32_t>(), g->sms, st));
+  CK(launch_setcover(P, g->sms * bps, st));
+  CK(cudaEventRecord(ws.e1, st));
+  CK(cudaMemcpyAsync(ws.h_sync.p, P.sync, sizeof(Sync), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ws.h_stats.p, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ws.h_kstate.p, P.ss, sizeof(ScState), cudaMemcpyDeviceToHost, st));
+  if (!dev_out)
+    CK(cudaMemcpyAsync(step_out, P.step_out, sizeof(uint32_t) * (size_t)n,
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ws.e0, ws.e1));
+  const Sync* hy = ws.h_sync.as<Sync>();
+  const ScState* hs = ws.h_kstate.as<ScState>();
+  Stats acc = *ws.h_stats.as<Stats>();
+  acc.v[15] = (unsigned long long)(ms * 1.0e6);
+  acc.v[kStFused] = hs->gathers;
+  export_stats(acc, 0, stats);
+  if (hy->err & kErrBounds) {
+    if (hy->bad_code == kScBadPriority) {
+      snprintf(g_cuda_msg, sizeof(g_cuda_msg),
+               "priority of set %u (%u) is out of range or repeated", hy->bad_val, hy->bad_aux);
+      return OG_E_INVALID;
+    }
     snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
              hy->bad_code, hy->bad_val, hy->bad_aux);
     return OG_E_INTERNAL;

@@ -49,12 +49,12 @@ def test_parser_defaults_and_workloads():
     assert (a.gpus, a.workload, a.warmup) == (1, "road-sssp", 3) and a.warmup >= 3
     assert a.impl == "ours" and a.side == 4900 and a.sources == 8
     for w in ("rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf", "road-lazy",
-              "rmat-lazy", "rmat-kcore"):
+              "rmat-lazy", "rmat-kcore", "rmat-setcover"):
         assert bench.parse_args(["--workload", w]).workload == w
 
 
 def test_reference_metrics_name_every_workload():
     choices = {"road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf",
-               "road-lazy", "rmat-lazy", "rmat-kcore"}
+               "road-lazy", "rmat-lazy", "rmat-kcore", "rmat-setcover"}
     assert set(bench.REF_METRIC) == choices
     assert "queries/s" in bench.REF_METRIC["batch"] and "GTEPS" in bench.REF_METRIC["road-sssp"]
