@@ -66,9 +66,6 @@ def parse_args(argv=None):
     p.add_argument("--fusion", type=int, default=0)
     p.add_argument("--tile", type=int, default=0, help="frontier tile (with --delta)")
     p.add_argument("--hub", type=int, default=0, help="hub out-degree (with --delta)")
-    p.add_argument("--local", type=int, default=0,
-                   help="set cover: elements of a step run on one CTA (0 = library default, "
-                        "-1 = never)")
     p.add_argument("--arena", type=int, default=0,
                    help="bucket entries per query (0 = library default)")
     p.add_argument("--cpu-sources", type=int, default=2,
@@ -858,8 +855,7 @@ def run_setcover(args):
     eps = 10000
     g = graphgen.rmat(args.scale, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
     G = og.Graph.from_csr(g)
-    local = {0: 0, -1: og.FUSION_OFF}.get(args.local, args.local)
-    cfg = og.config(hub_degree=args.hub, fusion_threshold=local) if (args.hub or local) else None
+    cfg = og.config(hub_degree=args.hub) if args.hub else None
     pri = graphgen.priorities(g.n, seed=1)
     dpri = torch.from_numpy(pri.view(np.int32)).cuda()
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
@@ -920,8 +916,6 @@ def run_setcover(args):
                                "adjacency lists, eps = 0.01, random priorities), one "
                                "persistent launch per step", "n": g.n, "m": g.m,
                    "hub_degree": args.hub or 32,
-                   "steps_on_one_cta_up_to_elements": "off" if args.local == -1 else
-                   (args.local or 2048),
                    "l2": "inputs larger than L2 (graph %.0f MB)" % (8 * g.m / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),
                      "peak": peak, "unit": "GB/s",
@@ -929,8 +923,7 @@ def run_setcover(args):
                      "peak_source": peak_kind, "kernel": "og_setcover_kernel",
                      "bytes_per_launch": bytes_step, "kernel_ms": round(kernel_s * 1e3, 3)},
         "setcover": {"sets_chosen": chosen, "steps": int(st.rounds),
-                     "steps_on_one_cta": int(st.fused_iters),
-                     "buckets": int(st.redistributions), "set_visits": int(st.items),
+                     "buckets": int(st.fused_iters), "set_visits": int(st.items),
                      "elements_scanned": int(st.relax), "moves": int(st.global_inserts),
                      "cta_time_share": {
                          k: round(v / max(1, st.t_frontier_ns + st.t_fused_ns + st.t_hub_ns

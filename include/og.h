@@ -252,17 +252,12 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* cfg, uint32_t* core_ou
  *        give the method's expected number of steps per bucket); NULL = the identity.
  *   cfg: NULL or a config; used fields: hub_degree (a set with at least this many
  *        uncovered elements has them split over every warp of the grid; 0 = 32; clamped
- *        to [16, 2^26]), fusion_threshold (a step, or a gather of a bucket's band, with
- *        at most this many elements runs on one CTA with no grid barrier, back to back
- *        with the steps after it -- the fusion of Section 3.3 applied to set cover;
- *        0 = 2048, OG_FUSION_OFF = never; the result does not depend on it),
- *        blocks_per_sm (0 = 2), spin_limit_ns.
+ *        to [16, 2^26]), blocks_per_sm (0 = 2), spin_limit_ns.
  *   step_out: uint32[n], host or device: the 1-based step in which set v joined the
  *        cover, 0 if it did not.
- *   stats (may be NULL): rounds = steps, fused_iters = steps run on one CTA,
- *        redistributions = buckets worked off, items = set visits, relax = elements
- *        scanned, improved = sets chosen, global_inserts = sets moved to a lower bucket,
- *        kernel_ns (including the set-up kernels), and summed
+ *   stats (may be NULL): rounds = steps, fused_iters = buckets worked off, items = set
+ *        visits, relax = elements scanned, improved = sets chosen, global_inserts = sets
+ *        moved to a lower bucket, kernel_ns (including the set-up kernels), and summed
  *        over CTAs: t_frontier_ns (pack and claim phases), t_fused_ns (count, join and
  *        cover phases), t_hub_ns (bucket gathers), t_barrier_ns.
  * Requirements: every out-degree below 2^30, m below 2^32, at most 2^22 buckets.

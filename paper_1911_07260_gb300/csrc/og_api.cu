@@ -182,7 +182,6 @@ constexpr uint32_t kHubChunks = 1u << 20;   // 1024-edge hub chunks per round
 constexpr uint32_t kKcoreHub = 256;         // k-core: default hub out-degree
 constexpr uint32_t kSetcoverHub = 32;       // set cover: residual size of a large set
 constexpr int kSetcoverBps = 2;             // set cover: default CTAs per SM
-constexpr uint32_t kSetcoverLocal = 2048;   // set cover: elements of a step run on one CTA
 constexpr int kKcoreBps = 2;                // k-core: default CTAs per SM
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 
@@ -1158,13 +1157,6 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   }
   P.lg_cap = lg_cap;
   P.hub = hub;
-  // Steps (and band gathers) of at most this many elements run on one CTA without grid
-  // barriers; OG_FUSION_OFF keeps every step on the grid.
-  uint32_t local = kSetcoverLocal;
-  if (ucfg && ucfg->fusion_threshold)
-    local = ucfg->fusion_threshold == OG_FUSION_OFF ? 0u : ucfg->fusion_threshold;
-  P.local_elems = local;
-  P.local_ns = std::min<uint64_t>(50000000ull, c.spin_limit_ns / 4);
   P.sync = ws.sync.as<Sync>();
   P.ss = ws.scstate.as<ScState>();
   P.stats = ws.stats.as<Stats>();
@@ -1196,8 +1188,7 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   const ScState* hs = ws.h_kstate.as<ScState>();
   Stats acc = *ws.h_stats.as<Stats>();
   acc.v[15] = (unsigned long long)(ms * 1.0e6);
-  acc.v[kStFused] = hs->local_steps;
-  acc.v[kStRedist] = hs->gathers;
+  acc.v[kStFused] = hs->gathers;
   export_stats(acc, 0, stats);
   if (hy->err & kErrBounds) {
     if (hy->bad_code == kScBadPriority) {

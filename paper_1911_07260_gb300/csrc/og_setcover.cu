@@ -15,10 +15,7 @@
 // elements split into 256-element chunks over every warp of the grid, which needs one
 // more grid barrier after the pack (A2: classify, claim) and after the count (C: join,
 // cover, move).  One cooperative persistent launch; phases are separated by a bounded
-// grid barrier whose last arriver decides the next phase (sc_decide).  A step (or a
-// band gather) with few elements runs on one CTA instead, back to back with the steps
-// after it, __syncthreads separating the phases (local_run): the fusion idea of
-// Section 3.3 applied to set cover, where most buckets hold a handful of sets.
+// grid barrier whose last arriver decides the next phase (sc_decide).
 #include "og_device.cuh"
 #include "og_setcover.cuh"
 
@@ -33,8 +30,6 @@ struct ScSmem {
   uint32_t nl;        // large members
   uint32_t tl;        // elements of the large members (the step's element space)
   uint32_t gn;        // gather: entries of the band's current buffer
-  uint32_t pending;   // local run: phase to start with
-  uint32_t lnext;     // local run: next phase, or kNoPhase to hand back to the grid
   unsigned long long t_bar, t_a, t_b, t_g;  // per-CTA phase time (thread 0)
 };
 
@@ -43,16 +38,9 @@ struct ScCnt {
 };
 
 enum LMode : int { kLPack = 0, kLClaim = 1, kLCount = 2, kLCover = 3 };
-constexpr uint32_t kNoPhase = 0xFFFFFFFFu;
 
-// The warps a phase is spread over: every warp of the grid, or those of one CTA.
-struct Warps {
-  uint32_t w0, nw;  // this warp's index, number of warps
-};
-__device__ __forceinline__ Warps grid_warps() {
-  return {(blockIdx.x * blockDim.x + threadIdx.x) >> 5, gridDim.x * (blockDim.x >> 5)};
-}
-__device__ __forceinline__ Warps cta_warps() { return {threadIdx.x >> 5, blockDim.x >> 5}; }
+__device__ __forceinline__ uint32_t gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ uint32_t nwarps() { return gridDim.x * (blockDim.x >> 5); }
 
 __device__ __forceinline__ uint32_t next_store(uint32_t s) { return s == 1u ? 2u : 1u; }
 
@@ -157,11 +145,7 @@ __device__ __forceinline__ void list_insert(const ScParams& P, uint32_t sel, boo
     if (m) {
       const uint32_t leader = (uint32_t)__ffs(m) - 1u;
       uint32_t at = 0;
-      const uint32_t tot = warp_sum(f ? d : 0u);
-      if (lane == leader) {
-        at = atomicAdd(&P.ss->ns[sel], (uint32_t)__popc(m));
-        atomicAdd(&P.ss->stot[sel], (unsigned long long)tot);
-      }
+      if (lane == leader) at = atomicAdd(&P.ss->ns[sel], (uint32_t)__popc(m));
       at = __shfl_sync(FULL, at, leader);
       if (f) {
         const uint32_t pos = at + (uint32_t)__popc(m & lanemask_lt());
@@ -423,10 +407,10 @@ __device__ __forceinline__ uint32_t chunks(uint32_t tl) {
 }
 
 // Phase C, per large member: join or stay, move.
-__device__ void large_settle(const ScParams& P, const ScSmem& S, ScCnt& C, Warps W) {
+__device__ void large_settle(const ScParams& P, const ScSmem& S, ScCnt& C) {
   const uint32_t lane = threadIdx.x & 31;
   const ScList& Lc = P.lg[S.csel];
-  for (uint32_t b0 = W.w0 * 32u; b0 < S.nl; b0 += W.nw * 32u) {
+  for (uint32_t b0 = gwarp() * 32u; b0 < S.nl; b0 += nwarps() * 32u) {
     const uint32_t i = b0 + lane;
     const bool valid = i < S.nl;
     uint32_t v = 0, lw = 0, D = 0, W = 0;
@@ -444,7 +428,7 @@ __device__ void large_settle(const ScParams& P, const ScSmem& S, ScCnt& C, Warps
 
 // ---- phases ----------------------------------------------------------------------------
 
-__device__ void gather_phase(const ScParams& P, const ScSmem& S, Warps W) {
+__device__ void gather_phase(const ScParams& P, const ScSmem& S) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t b = S.band;
   const uint32_t cap = __ldg(P.bcap + b);
@@ -452,7 +436,7 @@ __device__ void gather_phase(const ScParams& P, const ScSmem& S, Warps W) {
   const uint32_t cnt = min(S.gn, cap);
   const unsigned long long* src = P.bl + __ldg(P.bbase + b) + (unsigned long long)sel * cap;
   unsigned long long* dst = P.bl + __ldg(P.bbase + b) + (unsigned long long)(sel ^ 1u) * cap;
-  for (uint32_t b0 = W.w0 * 32u; b0 < cnt; b0 += W.nw * 32u) {
+  for (uint32_t b0 = gwarp() * 32u; b0 < cnt; b0 += nwarps() * 32u) {
     const uint32_t i = b0 + lane;
     const bool ok = i < cnt;
     const unsigned long long e = ok ? __ldcg(src + i) : 0ull;
@@ -478,44 +462,35 @@ __device__ void gather_phase(const ScParams& P, const ScSmem& S, Warps W) {
   }
 }
 
-__device__ void phase_a(const ScParams& P, const ScSmem& S, ScCnt& C, Warps W) {
+__device__ void phase_a(const ScParams& P, const ScSmem& S, ScCnt& C) {
   const uint32_t G = (S.ns + 31u) / 32u, K = S.nl ? chunks(S.tl) : 0u;
-  for (uint32_t u = W.w0; u < G + K; u += W.nw) {
+  for (uint32_t u = gwarp(); u < G + K; u += nwarps()) {
     if (u < G) small_a(P, S, u, C);
     else large_chunk(P, S, u - G, kLPack, C);
   }
 }
 
-__device__ void phase_a2(const ScParams& P, const ScSmem& S, ScCnt& C, Warps W) {
+__device__ void phase_a2(const ScParams& P, const ScSmem& S, ScCnt& C) {
   const uint32_t K = S.nl ? chunks(S.tl) : 0u;
-  for (uint32_t u = W.w0; u < K; u += W.nw) large_chunk(P, S, u, kLClaim, C);
+  for (uint32_t u = gwarp(); u < K; u += nwarps()) large_chunk(P, S, u, kLClaim, C);
 }
 
-__device__ void phase_b(const ScParams& P, const ScSmem& S, ScCnt& C, Warps W) {
+__device__ void phase_b(const ScParams& P, const ScSmem& S, ScCnt& C) {
   const uint32_t G = (S.ns + 31u) / 32u, K = S.nl ? chunks(S.tl) : 0u;
-  for (uint32_t u = W.w0; u < G + K; u += W.nw) {
+  for (uint32_t u = gwarp(); u < G + K; u += nwarps()) {
     if (u < G) small_b(P, S, u, C);
     else large_chunk(P, S, u - G, kLCount, C);
   }
 }
 
-__device__ void phase_c(const ScParams& P, const ScSmem& S, ScCnt& C, Warps W) {
+__device__ void phase_c(const ScParams& P, const ScSmem& S, ScCnt& C) {
   const uint32_t K = S.nl ? chunks(S.tl) : 0u;
-  for (uint32_t u = W.w0; u < K; u += W.nw) large_chunk(P, S, u, kLCover, C);
-  large_settle(P, S, C, W);
+  for (uint32_t u = gwarp(); u < K; u += nwarps()) large_chunk(P, S, u, kLCover, C);
+  large_settle(P, S, C);
 }
 
-__device__ void run_phase(const ScParams& P, const ScSmem& S, ScCnt& C, uint32_t phase, Warps W) {
-  if (phase == kScGather) gather_phase(P, S, W);
-  else if (phase == kScA) phase_a(P, S, C, W);
-  else if (phase == kScA2) phase_a2(P, S, C, W);
-  else if (phase == kScB) phase_b(P, S, C, W);
-  else if (phase == kScC) phase_c(P, S, C, W);
-}
-
-// The phase after `done`, with the state it needs (lane 0 writes it).  Run by one warp:
-// warp 0 of the CTA that arrives last at a grid barrier, or of the CTA of a local run.
-__device__ uint32_t sc_next(const ScParams& P, uint32_t done) {
+// Run by warp 0 of the CTA that arrives last at a grid barrier: the next phase.
+__device__ void sc_decide(const ScParams& P, uint32_t done) {
   const uint32_t lane = threadIdx.x & 31;
   ScState* ss = P.ss;
   const bool fatal = (ld_relaxed(&P.sync->err) & kErrFatal) != 0u;
@@ -537,7 +512,6 @@ __device__ uint32_t sc_next(const ScParams& P, uint32_t done) {
           ss->gmax = 0u;
           ss->gcnt = 0u;
           ss->ns[0] = ss->ns[1] = 0u;
-          ss->stot[0] = ss->stot[1] = 0ull;
           ss->bw[0] = ss->bw[1] = 0ull;
           ss->gathers = __ldcg(&ss->gathers) + 1u;
         }
@@ -598,7 +572,6 @@ __device__ uint32_t sc_next(const ScParams& P, uint32_t done) {
           if (lane == 0) {
             ss->csel = x;
             ss->ns[c] = 0u;
-            ss->stot[c] = 0ull;
             ss->bw[c] = 0ull;
           }
           next = start_step();
@@ -612,107 +585,7 @@ __device__ uint32_t sc_next(const ScParams& P, uint32_t done) {
     }
   }
   __syncwarp();
-  return next;
-}
-
-// Whether phase `next` (a new step, or a band gather) is small enough for a local run.
-// Lane 0 reads, every lane gets the answer.
-__device__ bool local_fits(const ScParams& P, uint32_t next) {
-  uint32_t fits = 0;
-  if ((threadIdx.x & 31) == 0 && P.local_elems) {
-    const ScState* ss = P.ss;
-    unsigned long long w = ~0ull;
-    if (next == kScA) {
-      const uint32_t c = __ldcg(&ss->csel) & 1u;
-      w = __ldcg(&ss->stot[c]) + (__ldcg(&ss->bw[c]) & kScTotMask);
-    } else if (next == kScGather) {
-      const uint32_t b = __ldcg(&ss->band);
-      if (b < P.nbands) w = __ldcg(P.bcnt + b);
-    }
-    fits = w <= P.local_elems ? 1u : 0u;
-  }
-  return __shfl_sync(FULL, fits, 0) != 0u;
-}
-
-// Run by warp 0 of the CTA that arrives last at a grid barrier: publishes the next phase
-// (after a local run, the phase it handed back).  A new step or band gather that is
-// small enough becomes a local run.
-__device__ void sc_decide(const ScParams& P, uint32_t done) {
-  const uint32_t lane = threadIdx.x & 31;
-  uint32_t next;
-  if (done == kScLocal) {
-    uint32_t p = 0;
-    if (lane == 0) p = __ldcg(&P.ss->pending);
-    next = __shfl_sync(FULL, p, 0);
-    if (ld_relaxed(&P.sync->err) & kErrFatal) next = kScStop;
-  } else {
-    next = sc_next(P, done);
-  }
-  if ((next == kScA || next == kScGather) && local_fits(P, next)) {
-    if (lane == 0) P.ss->pending = next;
-    next = kScLocal;
-  }
-  __syncwarp();
   if (lane == 0) P.sync->phase = next;
-}
-
-// Thread 0: the state the phases read, from the global state words.
-__device__ void load_state(const ScParams& P, ScSmem& S) {
-  S.err = ld_relaxed(&P.sync->err);
-  const ScState* ss = P.ss;
-  S.j = __ldcg(&ss->j);
-  S.step = __ldcg(&ss->step);
-  S.csel = __ldcg(&ss->csel) & 1u;
-  S.band = __ldcg(&ss->band);
-  S.pending = __ldcg(&ss->pending);
-  S.ns = min(__ldcg(&ss->ns[S.csel]), P.n);
-  const unsigned long long bw = __ldcg(&ss->bw[S.csel]);
-  S.nl = (uint32_t)min(bw >> kScCntShift, (unsigned long long)P.lg_cap);
-  S.tl = (uint32_t)min(bw & kScTotMask, 0xFFFFFFFFull);
-  const uint32_t jj = S.j < P.nb ? S.j : 0u;
-  S.tj = P.nb ? __ldg(P.t + jj) : 1u;
-  S.tauj = P.nb ? __ldg(P.tau + jj) : 1u;
-  S.gn = S.band < P.nbands ? __ldcg(P.bcnt + S.band) : 0u;
-}
-
-__device__ __forceinline__ void add_time(ScSmem& S, uint32_t phase, uint64_t dt) {
-  if (phase == kScGather) S.t_g += dt;
-  else if (phase == kScA || phase == kScA2) S.t_a += dt;
-  else S.t_b += dt;
-}
-
-// One CTA runs the phases from S.pending on, deciding each next phase itself, while
-// the steps and gathers stay small; then it leaves the next phase in ss->pending for
-// the grid.  Bounded by local_ns and kScLocalMax phases.
-__device__ void local_run(const ScParams& P, ScSmem& S, ScCnt& C) {
-  const Warps W = cta_warps();
-  const uint64_t t_begin = threadIdx.x == 0 ? gtimer() : 0ull;
-  uint32_t phase = S.pending;
-  for (uint32_t n = 0;; ++n) {
-    const uint64_t t0 = threadIdx.x == 0 ? gtimer() : 0ull;
-    run_phase(P, S, C, phase, W);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint64_t now = gtimer();
-      add_time(S, phase, now - t0);
-      if (phase == kScA) P.ss->local_steps += 1u;
-    }
-    if (threadIdx.x < 32) {
-      const uint32_t next = sc_next(P, phase);
-      const uint64_t spent = __shfl_sync(FULL, threadIdx.x == 0 ? gtimer() - t_begin : 0ull, 0);
-      bool go = next != kScStop && spent < P.local_ns && n + 1u < kScLocalMax;
-      if (go && (next == kScA || next == kScGather)) go = local_fits(P, next);
-      if (threadIdx.x == 0) {
-        S.lnext = go ? next : kNoPhase;
-        if (!go) P.ss->pending = next;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) load_state(P, S);
-    __syncthreads();
-    if (S.lnext == kNoPhase) break;
-    phase = S.lnext;
-  }
 }
 
 // Bounded grid barrier: the last CTA to arrive runs sc_decide and releases the others,
@@ -750,7 +623,20 @@ __device__ void sc_barrier(const ScParams& P, ScSmem& S, uint32_t& bar, uint32_t
   __syncthreads();
   if (threadIdx.x == 0) {
     S.phase = ld_acquire(&P.sync->phase);
-    load_state(P, S);
+    S.err = ld_relaxed(&P.sync->err);
+    const ScState* ss = P.ss;
+    S.j = __ldcg(&ss->j);
+    S.step = __ldcg(&ss->step);
+    S.csel = __ldcg(&ss->csel) & 1u;
+    S.band = __ldcg(&ss->band);
+    S.ns = min(__ldcg(&ss->ns[S.csel]), P.n);
+    const unsigned long long bw = __ldcg(&ss->bw[S.csel]);
+    S.nl = (uint32_t)min(bw >> kScCntShift, (unsigned long long)P.lg_cap);
+    S.tl = (uint32_t)min(bw & kScTotMask, 0xFFFFFFFFull);
+    const uint32_t jj = S.j < P.nb ? S.j : 0u;
+    S.tj = P.nb ? __ldg(P.t + jj) : 1u;
+    S.tauj = P.nb ? __ldg(P.tau + jj) : 1u;
+    S.gn = S.band < P.nbands ? __ldcg(P.bcnt + S.band) : 0u;
     S.t_bar += gtimer() - t_in;
   }
   __syncthreads();
@@ -768,12 +654,17 @@ extern "C" __global__ void __launch_bounds__(kBlock, 4) og_setcover_kernel(ScPar
   for (;;) {
     const uint32_t phase = S.phase;
     if (phase == kScStop || (S.err & kErrFatal)) break;
-    if (phase == kScLocal) {
-      if (blockIdx.x == 0) local_run(P, S, C);
-    } else {
-      const uint64_t t0 = threadIdx.x == 0 ? gtimer() : 0ull;
-      run_phase(P, S, C, phase, grid_warps());
-      if (threadIdx.x == 0) add_time(S, phase, gtimer() - t0);
+    const uint64_t t0 = threadIdx.x == 0 ? gtimer() : 0ull;
+    if (phase == kScGather) gather_phase(P, S);
+    else if (phase == kScA) phase_a(P, S, C);
+    else if (phase == kScA2) phase_a2(P, S, C);
+    else if (phase == kScB) phase_b(P, S, C);
+    else if (phase == kScC) phase_c(P, S, C);
+    if (threadIdx.x == 0) {
+      const uint64_t dt = gtimer() - t0;
+      if (phase == kScGather) S.t_g += dt;
+      else if (phase == kScA || phase == kScA2) S.t_a += dt;
+      else S.t_b += dt;
     }
     sc_barrier(P, S, bar, phase);
   }

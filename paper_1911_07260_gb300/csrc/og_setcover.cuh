@@ -32,7 +32,6 @@ constexpr uint32_t kScMaxHub = 1u << 26;     // a group of 32 small sets spans <
 constexpr uint32_t kScMaxBuckets = 1u << 22;
 constexpr uint32_t kScCntShift = 36;         // large lists: (entries << 36) | elements
 constexpr unsigned long long kScTotMask = (1ull << kScCntShift) - 1ull;
-constexpr uint32_t kScLocalMax = 1u << 16;   // phases of one local run at most
 
 enum ScPhase : uint32_t {
   kScGather = 0,    // band entries of bucket j -> member lists; the rest compacted
@@ -44,10 +43,6 @@ enum ScPhase : uint32_t {
   kScC = 4,         // large sets: join or stay, cover, move
   kScStop = 5,
   kScPrologue = 6,
-  kScLocal = 7,     // one CTA runs steps (and gathers of small bands) back to back with
-                    // __syncthreads in place of grid barriers, while the step's work is
-                    // below local_elems (the fusion idea of Section 3.3 applied to the
-                    // steps of set cover); the other CTAs wait at the next grid barrier
 };
 
 // Members of the current bucket (a step reads one pair of lists and appends the sets
@@ -70,9 +65,6 @@ struct ScState {
   uint32_t gmax;            // gather: largest bucket among the band entries kept
   uint32_t gcnt;            // gather: band entries kept
   uint32_t gathers;         // buckets gathered
-  uint32_t pending;         // phase to run next when a local run ends (or starts)
-  unsigned long long stot[2];  // small member lists: elements
-  uint32_t local_steps;     // steps run by a local run
   uint32_t pad;
 };
 
@@ -101,8 +93,6 @@ struct ScParams {
   ScList sm[2], lg[2];          // small / large member lists
   uint32_t lg_cap;
   uint32_t hub;                 // residual size from which a set is large
-  uint32_t local_elems;         // a step (or band gather) this small runs on one CTA; 0 = never
-  unsigned long long local_ns;  // a local run hands back to the grid after this long
   Sync* sync;
   ScState* ss;
   Stats* stats;

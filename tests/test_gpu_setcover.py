@@ -97,28 +97,6 @@ def test_setcover_launch_shapes_identical(og, orc, gg, hub, bps):
     assert st.rounds == steps
 
 
-@pytest.mark.parametrize("local", ["off", 1, 64, 0, 0xFFFFFFFF])
-@pytest.mark.parametrize("eps", [0, 10000])
-def test_setcover_local_runs_identical(og, orc, gg, local, eps):
-    """Steps and band gathers small enough run on one CTA with no grid barrier (the
-    fusion idea applied to set cover); any threshold -- never, tiny, the default, every
-    step on one CTA -- gives the oracle's cover and step count."""
-    thr = og.FUSION_OFF if local == "off" else local
-    cfg = og.config(fusion_threshold=thr) if thr else None
-    for name, g in _graphs(gg):
-        if name == "grid64":
-            continue
-        pri = gg.priorities(g.n, seed=3 + len(name))
-        ref, steps = orc.setcover(g, pri, eps)
-        got, st = og.setcover(og.Graph.from_csr(g), eps, pri, cfg=cfg)
-        np.testing.assert_array_equal(got, ref, err_msg=name)
-        assert st.rounds == steps, name
-        if local == "off":
-            assert st.fused_iters == 0, name
-        elif local == 0xFFFFFFFF and steps:
-            assert st.fused_iters > 0, name
-
-
 def test_setcover_identity_priorities_and_device_buffers(og, orc, gg):
     """NULL priorities are the identity; device priorities and a device output give the
     host result."""
