@@ -282,3 +282,68 @@ def test_kcore_level_sets_are_cores(gg, orc):
         at_k = core[src] == k
         cnt = np.bincount(src[at_k & up], minlength=g.n)
         assert (cnt[core == k] <= k).all()
+
+
+# ---- k-core mutants: plausible mistakes planted in a copy of the oracle's source ---------
+
+# The floor at the level k and the level that only rises each keep the result exact on
+# their own (a priority never falls below k, so the level never has to fall), so removing
+# one of them alone changes nothing; the mistake is losing both.
+_KCORE_MUTANTS = {
+    # neighbours lowered below the current level and the level following them down
+    "no_floor_level_drops": [("if (done[w] || prio[w] <= k) continue;",
+                              "if (done[w] || prio[w] == 0) continue;"),
+                             ("if (prio[v] > k) k = prio[v];", "k = prio[v];")],
+    # a neighbour loses two per extracted vertex instead of one
+    "double_decrement": [("prio[w] -= 1;", "prio[w] -= (prio[w] > k + 1) ? 2 : 1;")],
+    # the level set from the neighbour count instead of the extracted priority
+    "level_from_degree": [("if (prio[v] > k) k = prio[v];",
+                           "if (off[v + 1] - off[v] > k) k = (uint32_t)(off[v + 1] - off[v]);")],
+}
+
+_KCORE_RUNNER = r"""
+import ctypes, itertools, sys, numpy as np
+sys.path.insert(0, sys.argv[2])
+import graphgen as gg
+from tests.test_oracle_pins import _core_brute
+L = ctypes.CDLL(sys.argv[1])
+vp, u32 = ctypes.c_void_p, ctypes.c_uint32
+L.or_kcore.argtypes = [u32, vp, vp, vp]
+bad = 0
+for seed in range(12):
+    rng = np.random.default_rng(seed)
+    n = 9
+    p = 0.15 + 0.07 * seed
+    pairs = [(u, v) for u, v in itertools.combinations(range(n), 2) if rng.random() < p]
+    s = [u for u, v in pairs] + [v for u, v in pairs]
+    d = [v for u, v in pairs] + [u for u, v in pairs]
+    g = gg.from_edges(n, s, d, [1] * len(s))
+    off = np.ascontiguousarray(g.offsets, np.uint64)
+    nbr = np.ascontiguousarray(g.nbr, np.uint32)
+    out = np.empty(n, np.uint32)
+    L.or_kcore(n, off.ctypes.data, nbr.ctypes.data, out.ctypes.data)
+    bad += out.tolist() != _core_brute(n, pairs)
+print(bad)
+"""
+
+
+@pytest.mark.parametrize("name", sorted(_KCORE_MUTANTS))
+def test_kcore_pins_reject_planted_mistakes(gg, orc, tmp_path, name):
+    """Each mutant of or_kcore (compiled from a patched copy of oracle.c) must disagree
+    with the coreness definition (subset brute force) on some of the random graphs."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "oracle", "oracle.c")).read()
+    for old, new in _KCORE_MUTANTS[name]:
+        assert src.count(old) == 1, name
+        src = src.replace(old, new)
+    c = tmp_path / "mutant.c"
+    c.write_text(src)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(c)],
+                   check=True)
+    r = subprocess.run([sys.executable, "-c", _KCORE_RUNNER, str(so), root],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 or int(r.stdout.strip().splitlines()[-1]) > 0, name
