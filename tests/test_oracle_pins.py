@@ -347,3 +347,82 @@ def test_kcore_pins_reject_planted_mistakes(gg, orc, tmp_path, name):
     r = subprocess.run([sys.executable, "-c", _KCORE_RUNNER, str(so), root],
                        capture_output=True, text=True, timeout=120)
     assert r.returncode != 0 or int(r.stdout.strip().splitlines()[-1]) > 0, name
+
+
+# ---- Dijkstra mutants ---------------------------------------------------------------------
+
+_DIJKSTRA_MUTANTS = {
+    # the heap orders by the largest key (the comparison of a push reversed)
+    "max_heap_push": [("if (h[p].key <= x.key) break;", "if (h[p].key >= x.key) break;")],
+    # each edge takes the weight of the next edge in the array
+    "shifted_weight": [("      uint64_t nd = d[u] + w[e];\n      if (nd < d[v]) {",
+                        "      uint64_t nd = d[u] + w[e + 1 < m ? e + 1 : e];\n"
+                        "      if (nd < d[v]) {")],
+    # a vertex keeps the label of its first discovery (no decrease of a known distance)
+    "first_label_only": [("      uint64_t nd = d[u] + w[e];\n      if (nd < d[v]) {",
+                          "      uint64_t nd = d[u] + w[e];\n      if (d[v] == UINT64_MAX) {")],
+}
+
+_DIJKSTRA_RUNNER = r"""
+import ctypes, sys, numpy as np
+sys.path.insert(0, sys.argv[2])
+import graphgen as gg
+from tests.test_oracle_pins import _brute, _edges_of
+L = ctypes.CDLL(sys.argv[1])
+vp, u32 = ctypes.c_void_p, ctypes.c_uint32
+L.or_dijkstra.argtypes = [u32, vp, vp, vp, u32, u32, vp]
+bad = 0
+for seed in range(40):
+    g = gg.random_graph(7, 14, wlo=1, whi=20, seed=seed, self_loops=False)
+    off = np.ascontiguousarray(g.offsets, np.uint64)
+    nbr = np.ascontiguousarray(g.nbr, np.uint32)
+    w = np.ascontiguousarray(g.w, np.uint32)
+    out = np.empty(g.n, np.uint32)
+    L.or_dijkstra(g.n, off.ctypes.data, nbr.ctypes.data, w.ctypes.data, 0, 0xFFFFFFFF,
+                  out.ctypes.data)
+    bad += out.tolist() != _brute(g.n, _edges_of(g), 0)
+print(bad)
+"""
+
+
+@pytest.mark.parametrize("name", sorted(_DIJKSTRA_MUTANTS))
+def test_dijkstra_pins_reject_planted_mistakes(gg, orc, tmp_path, name):
+    """Each mutant of or_dijkstra (a patched copy of oracle.c) must disagree with the
+    brute-force minimum over simple paths on some of 40 random graphs."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "oracle", "oracle.c")).read()
+    for old, new in _DIJKSTRA_MUTANTS[name]:
+        assert src.count(old) == 1, name
+        src = src.replace(old, new)
+    c = tmp_path / "mutant.c"
+    c.write_text(src)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(c)],
+                   check=True)
+    r = subprocess.run([sys.executable, "-c", _DIJKSTRA_RUNNER, str(so), root],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 or int(r.stdout.strip().splitlines()[-1]) > 0, name
+
+
+@pytest.mark.parametrize("runner", ["kcore", "dijkstra", "setcover"])
+def test_mutant_runners_accept_the_unmodified_oracle(gg, orc, tmp_path, runner):
+    """Control for the planted-mistake tests: the unmodified oracle, compiled the same way
+    and run by the same runner, exits 0 and disagrees with nothing (so a mutant counts as
+    caught only for what it changed, not for a broken runner)."""
+    import os
+    import subprocess
+    import sys
+    from tests import test_oracle_setcover as tsc
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = tmp_path / "libplain.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so),
+                    os.path.join(root, "oracle", "oracle.c")], check=True)
+    code = {"kcore": _KCORE_RUNNER, "dijkstra": _DIJKSTRA_RUNNER,
+            "setcover": tsc._RUNNER}[runner]
+    r = subprocess.run([sys.executable, "-c", code, str(so), root], capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-500:]
+    assert int(r.stdout.strip().splitlines()[-1]) == 0
