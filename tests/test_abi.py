@@ -82,3 +82,16 @@ def test_struct_fields_match_header(og):
 def test_library_does_not_link_the_oracle(og):
     data = open(og.LIB_PATH, "rb").read()
     assert b"or_dijkstra" not in data and b"liboracle" not in data
+
+
+def test_null_arguments_are_rejected_before_any_device_call(og):
+    """Entry points validate their arguments on the host first: a NULL graph or output, a
+    bad mode or eps returns OG_E_INVALID without touching a GPU (none is present here)."""
+    L = og.lib()
+    out = (ctypes.c_uint32 * 4)()
+    assert L.og_setcover(None, 10000, None, None, out, None, None) == og.E_INVALID
+    assert L.og_kcore(None, 0, None, out, None, None) == og.E_INVALID
+    fake = ctypes.c_void_p(1)  # never dereferenced: the bad eps / mode is checked first
+    assert L.og_setcover(fake, 1000001, None, None, out, None, None) == og.E_INVALID
+    assert L.og_setcover(fake, 10000, None, None, None, None, None) == og.E_INVALID
+    assert L.og_kcore(fake, 7, None, out, None, None) == og.E_INVALID
