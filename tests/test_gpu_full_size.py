@@ -1,13 +1,20 @@
-"""GPU parity at the benchmarked full size, in the launch configuration bench.py times.
+"""GPU parity at the benchmarked full sizes, in the launch configurations bench.py times.
 
-The default workload: the road-like 4900 x 4900 grid (23,997,150 vertices, 82,565,692
-directed edges, every weight >= 100) and the bench's 8 seeded sources in one persistent
-batch launch (`og_batch_run`), under the library's default schedule and under the
-schedule the autotuner picks for this graph (Delta 4096, fusion threshold 1024, tile 32).
-Every source's distance array passes the oracle's certificate check -- dist[src] = 0,
-no edge can improve a distance, every reached vertex has a tight in-edge -- which with
-positive weights holds for the exact shortest-path distances only; two of the sources
-are also compared element by element with the oracle's Dijkstra.
+* The default workload: the road-like 4900 x 4900 grid (23,997,150 vertices, 82,565,692
+  directed edges, every weight >= 100) and the bench's 8 seeded sources in one
+  persistent batch launch (`og_batch_run`), under the library's default schedule and
+  under the schedule the autotuner picks for this graph (Delta 4096, fusion threshold
+  1024, tile 32). Every source's distance array passes the oracle's certificate check
+  -- dist[src] = 0, no edge can improve a distance, every reached vertex has a tight
+  in-edge -- which with positive weights holds for the exact shortest-path distances
+  only; two of the sources are also compared element by element with the oracle's
+  Dijkstra.
+* R-MAT scale 24 (16,777,216 vertices, 520,762,674 directed edges, weights in
+  [1, 2^16)) with the bench's 8 sources and its tuned schedule (Delta 256, fusion off,
+  tile 256): the certificate on two sources (a Dijkstra there takes ~40 s a source).
+* Set cover on the same R-MAT graph (its structure does not depend on the weight range,
+  and set cover ignores weights, so it is the `rmat-setcover` workload): the chosen sets
+  cover every element, and another launch shape chooses the same sets in the same steps.
 """
 import numpy as np
 import pytest
@@ -43,3 +50,47 @@ def test_full_size_road_batch_vs_oracle(og, orc):
             assert orc.check_sssp(g, int(s), d[i]) == (0, 0), (i, cfg)
         for i, r in ref.items():
             np.testing.assert_array_equal(d[i], r)
+    del out
+    G.free()
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    import bench
+    g, _, srcs = bench.build_workload(bench.parse_args(["--workload", "rmat-sssp"]), 0, 1)
+    assert (g.n, g.m, len(srcs)) == (16777216, 520762674, 8)
+    return g, srcs
+
+
+def test_full_size_rmat_sssp_batch_certified(og, orc, rmat24):
+    import torch
+    g, srcs = rmat24
+    assert int(g.w.min()) >= 1
+    G = og.Graph.from_csr(g)
+    queries = [(og.Q_SSSP, int(s), 0, 0) for s in srcs]
+    out = torch.empty(len(queries) * g.n, dtype=torch.int32, device="cuda")
+    cfg = og.config(delta=256, fusion_threshold=og.FUSION_OFF, expand_tile=256)
+    og.batch_run(G, queries, cfg=cfg, out=out)
+    d = out.cpu().numpy().view(np.uint32).reshape(len(queries), g.n)
+    for i in (0, len(srcs) - 1):
+        assert orc.check_sssp(g, int(srcs[i]), d[i]) == (0, 0), i
+    del out
+    G.free()
+
+
+def test_full_size_rmat_setcover(og, gg, rmat24):
+    g, _ = rmat24
+    G = og.Graph.from_csr(g)
+    pri = gg.priorities(g.n, seed=1)
+    a, st = og.setcover(G, 10000, pri)
+    b, _ = og.setcover(G, 10000, pri, cfg=og.config(hub_degree=16, blocks_per_sm=1))
+    np.testing.assert_array_equal(a, b)
+    deg = np.diff(g.offsets).astype(np.int64)
+    chosen = np.repeat(a > 0, deg)
+    covered = np.zeros(g.n, bool)
+    covered[g.nbr[chosen]] = True
+    universe = np.zeros(g.n, bool)
+    universe[g.nbr] = True
+    assert (covered == universe).all()
+    assert 0 < st.rounds <= g.n and st.improved == int((a > 0).sum())
+    G.free()

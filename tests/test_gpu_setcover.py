@@ -146,23 +146,3 @@ def test_setcover_rejects_bad_arguments(og, gg):
     # the graph stays usable after a rejected call
     got, _ = og.setcover(G, 10000, np.arange(5))
     assert set(np.nonzero(got)[0].tolist()) >= {1}
-
-
-def test_setcover_full_size_rmat24_properties(og, gg):
-    """R-MAT scale 24 (the benchmarked workload, default launch shape): the chosen sets
-    cover every element, and another launch shape (one CTA per SM, sets of 16 or more
-    uncovered elements split over the grid) chooses the same sets in the same steps."""
-    g = gg.rmat(24, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
-    G = og.Graph.from_csr(g)
-    pri = gg.priorities(g.n, seed=1)
-    a, st = og.setcover(G, 10000, pri)
-    b, _ = og.setcover(G, 10000, pri, cfg=og.config(hub_degree=16, blocks_per_sm=1))
-    np.testing.assert_array_equal(a, b)
-    deg = np.diff(g.offsets).astype(np.int64)
-    chosen = np.repeat(a > 0, deg)
-    covered = np.zeros(g.n, bool)
-    covered[g.nbr[chosen]] = True
-    universe = np.zeros(g.n, bool)
-    universe[g.nbr] = True
-    assert (covered == universe).all()
-    assert 0 < st.rounds <= g.n and st.improved == int((a > 0).sum())
