@@ -59,6 +59,8 @@ def _load():
         L.or_kcore.argtypes = [u32, vp, vp, vp]
         L.or_setcover.restype = ctypes.c_int
         L.or_setcover.argtypes = [u32, vp, vp, u32, vp, vp, vp]
+        L.or_check_setcover.restype = ctypes.c_int
+        L.or_check_setcover.argtypes = [u32, vp, vp, u32, vp, ctypes.c_uint64, vp]
         _lib = L
     return _lib
 
@@ -148,3 +150,18 @@ def setcover(g, pri, eps_ppm: int = 10000) -> tuple[np.ndarray, int]:
     _status(_load().or_setcover(g.n, off.ctypes.data, nbr.ctypes.data, int(eps_ppm),
                                 p.ctypes.data, out.ctypes.data, ctypes.byref(steps)), False)
     return out, int(steps.value)
+
+
+def check_setcover(g, step_out, steps: int, eps_ppm: int = 10000) -> tuple[int, int]:
+    """Certificate of a set cover given as join steps (``oracle.c``,
+    ``or_check_setcover``).  Returns (code, where): 0 = certified; 1 = an element of the
+    universe stays uncovered (where = element); 2 = a set joined with too few new
+    elements (where = set); 3 = the sets of a step overlap too much (where = step);
+    4 = a step number beyond ``steps`` (where = set)."""
+    off, nbr, _ = _csr(g)
+    s = np.ascontiguousarray(step_out, dtype=np.uint32)
+    bad = ctypes.c_uint32(0)
+    code = _load().or_check_setcover(g.n, off.ctypes.data, nbr.ctypes.data, int(eps_ppm),
+                                     s.ctypes.data, int(steps), ctypes.byref(bad))
+    _status(code if code < 0 else 0, False)
+    return int(code), int(bad.value)

@@ -52,6 +52,15 @@
  *                       certificates of the approximate greedy choice, the near
  *                       independence and the (1 + eps)^2 H(max |S|) approximation bound
  *                       against brute-force optima.
+ *   - or_check_setcover: certificate of a set cover given as join steps: replays the
+ *                       steps in order and checks that every set that joins covers at
+ *                       least one and at least (largest residual) / (1 + eps)^2 new
+ *                       elements, that the sets of one step together cover at least that
+ *                       much each (they are nearly independent), and that the result
+ *                       covers the universe -- what the method guarantees, whatever its
+ *                       priorities.  Residuals are kept current through the reverse
+ *                       adjacency and a count per residual size, so the check is
+ *                       O(n + m + steps) rather than a rescan per step.
  *
  * Conventions.  Distances are uint32 with 0xFFFFFFFF = unreachable (the paper's INT_MAX
  * initialisation, Section 4.1).  A finite distance >= 0xFFFFFFFE cannot be represented;
@@ -397,4 +406,111 @@ int or_setcover(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t e
   *steps_out = step;
   free(t); free(head); free(nxt); free(mem); free(act); free(join); free(claim); free(cov);
   return OR_OK;
+}
+
+int or_check_setcover(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t eps_ppm,
+                      const uint32_t *step_out, uint64_t steps, uint32_t *bad) {
+  if (n == 0 || eps_ppm > 1000000u) return OR_INVALID;
+  *bad = 0;
+  const uint64_t m = off[n];
+  for (uint32_t v = 0; v < n; ++v)
+    if (step_out[v] > steps) { *bad = v; return 4; }
+  uint64_t maxdeg = 0;
+  for (uint32_t v = 0; v < n; ++v)
+    if (off[v + 1] - off[v] > maxdeg) maxdeg = off[v + 1] - off[v];
+  /* reverse adjacency: the sets holding element u, one entry per occurrence */
+  uint64_t *roff = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+  uint32_t *rset = (uint32_t *)malloc(sizeof(uint32_t) * (m ? m : 1));
+  uint64_t *fill = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  uint64_t *res = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  uint64_t *cnt = (uint64_t *)calloc(maxdeg + 1, sizeof(uint64_t));
+  uint64_t *soff = (uint64_t *)calloc(steps + 2, sizeof(uint64_t));
+  uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  unsigned char *cov = (unsigned char *)calloc(n, 1);
+  unsigned char *chosen = (unsigned char *)calloc(n, 1);
+  uint64_t *mark = (uint64_t *)calloc(n, sizeof(uint64_t));
+  int rc = 0;
+  if (!roff || !rset || !fill || !res || !cnt || !soff || !order || !cov || !chosen || !mark) {
+    rc = OR_NOMEM;
+    goto done;
+  }
+  for (uint64_t e = 0; e < m; ++e) roff[nbr[e] + 1]++;
+  for (uint32_t u = 0; u < n; ++u) roff[u + 1] += roff[u];
+  for (uint32_t u = 0; u < n; ++u) fill[u] = roff[u];
+  for (uint32_t v = 0; v < n; ++v)
+    for (uint64_t e = off[v]; e < off[v + 1]; ++e) rset[fill[nbr[e]]++] = v;
+  /* residual = uncovered entries of each set not chosen yet; cnt[r] = such sets */
+  for (uint32_t v = 0; v < n; ++v) {
+    res[v] = off[v + 1] - off[v];
+    cnt[res[v]]++;
+  }
+  uint64_t top = maxdeg;
+  /* the sets of each step, in step order */
+  for (uint32_t v = 0; v < n; ++v) soff[step_out[v] + 1]++;
+  for (uint64_t s = 0; s <= steps; ++s) soff[s + 1] += soff[s];
+  for (uint32_t v = 0; v < n; ++v) fill[v] = 0;
+  {
+    uint64_t *pos = (uint64_t *)malloc(sizeof(uint64_t) * (steps + 1));
+    if (!pos) { rc = OR_NOMEM; goto done; }
+    for (uint64_t s = 0; s <= steps; ++s) pos[s] = soff[s];
+    for (uint32_t v = 0; v < n; ++v) order[pos[step_out[v]]++] = v;
+    free(pos);
+  }
+  const unsigned __int128 R = (unsigned __int128)(1000000ull + eps_ppm) * (1000000ull + eps_ppm);
+  const unsigned __int128 MM = (unsigned __int128)1000000ull * 1000000ull;
+  for (uint64_t s = 1; s <= steps; ++s) {
+    const uint64_t b = soff[s], e_ = soff[s + 1];
+    if (b == e_) continue;
+    while (top > 0 && cnt[top] == 0) --top;
+    const uint64_t maxres = top;
+    uint64_t fresh = 0;
+    for (uint64_t i = b; i < e_; ++i) {
+      const uint32_t v = order[i];
+      if (res[v] == 0 || (unsigned __int128)res[v] * R < (unsigned __int128)maxres * MM) {
+        *bad = v;
+        rc = 2;
+        goto done;
+      }
+      for (uint64_t k = off[v]; k < off[v + 1]; ++k) {
+        const uint32_t u = nbr[k];
+        if (!cov[u] && mark[u] != s) {
+          mark[u] = s;
+          ++fresh;
+        }
+      }
+    }
+    if ((unsigned __int128)fresh * R <
+        (unsigned __int128)(e_ - b) * (unsigned __int128)maxres * MM) {
+      *bad = (uint32_t)s;
+      rc = 3;
+      goto done;
+    }
+    /* apply the step: the chosen sets leave, their new elements are covered */
+    for (uint64_t i = b; i < e_; ++i) {
+      const uint32_t v = order[i];
+      cnt[res[v]]--;
+      chosen[v] = 1;
+    }
+    for (uint64_t i = b; i < e_; ++i) {
+      const uint32_t v = order[i];
+      for (uint64_t k = off[v]; k < off[v + 1]; ++k) {
+        const uint32_t u = nbr[k];
+        if (cov[u]) continue;
+        cov[u] = 1;
+        for (uint64_t r = roff[u]; r < roff[u + 1]; ++r) {
+          const uint32_t w = rset[r];
+          if (chosen[w]) continue;
+          cnt[res[w]]--;
+          res[w]--;
+          cnt[res[w]]++;
+        }
+      }
+    }
+  }
+  for (uint32_t u = 0; u < n; ++u)
+    if (roff[u + 1] > roff[u] && !cov[u]) { *bad = u; rc = 1; goto done; }
+done:
+  free(roff); free(rset); free(fill); free(res); free(cnt); free(soff); free(order);
+  free(cov); free(chosen); free(mark);
+  return rc;
 }

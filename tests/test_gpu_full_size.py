@@ -13,8 +13,8 @@
   [1, 2^16)) with the bench's 8 sources and its tuned schedule (Delta 256, fusion off,
   tile 256): the certificate on two sources (a Dijkstra there takes ~40 s a source).
 * Set cover on the same R-MAT graph (its structure does not depend on the weight range,
-  and set cover ignores weights, so it is the `rmat-setcover` workload): the chosen sets
-  cover every element, and another launch shape chooses the same sets in the same steps.
+  and set cover ignores weights, so it is the `rmat-setcover` workload), in the bench's
+  launch shape and another one: every set's join step equals the oracle's.
 """
 import numpy as np
 import pytest
@@ -78,19 +78,14 @@ def test_full_size_rmat_sssp_batch_certified(og, orc, rmat24):
     G.free()
 
 
-def test_full_size_rmat_setcover(og, gg, rmat24):
+def test_full_size_rmat_setcover(og, orc, gg, rmat24):
     g, _ = rmat24
     G = og.Graph.from_csr(g)
     pri = gg.priorities(g.n, seed=1)
     a, st = og.setcover(G, 10000, pri)
     b, _ = og.setcover(G, 10000, pri, cfg=og.config(hub_degree=16, blocks_per_sm=1))
-    np.testing.assert_array_equal(a, b)
-    deg = np.diff(g.offsets).astype(np.int64)
-    chosen = np.repeat(a > 0, deg)
-    covered = np.zeros(g.n, bool)
-    covered[g.nbr[chosen]] = True
-    universe = np.zeros(g.n, bool)
-    universe[g.nbr] = True
-    assert (covered == universe).all()
-    assert 0 < st.rounds <= g.n and st.improved == int((a > 0).sum())
     G.free()
+    ref, steps = orc.setcover(g, pri, 10000)  # ~40 s on one core
+    np.testing.assert_array_equal(a, ref)
+    np.testing.assert_array_equal(b, ref)
+    assert st.rounds == steps and st.improved == int((ref > 0).sum())

@@ -329,3 +329,63 @@ def test_pins_reject_planted_mistakes(gg, orc, tmp_path, name):
     except subprocess.TimeoutExpired:
         caught = True  # the mutant never finishes: not a correct cover either
     assert caught, name
+
+
+# ---- the fast certificate (or_check_setcover) against the replay above --------------------
+
+def _perturb(s, rng):
+    """A plausible wrong answer: a chosen set dropped, moved to another step, an unchosen
+    set added to a step, or two sets' steps swapped."""
+    s = s.copy()
+    chosen = np.nonzero(s)[0]
+    other = np.nonzero(s == 0)[0]
+    k = int(s.max()) if s.size else 0
+    kind = rng.integers(4)
+    if kind == 0 and chosen.size:
+        s[rng.choice(chosen)] = 0
+    elif kind == 1 and chosen.size and k > 1:
+        s[rng.choice(chosen)] = rng.integers(1, k + 1)
+    elif kind == 2 and other.size and k:
+        s[rng.choice(other)] = rng.integers(1, k + 1)
+    elif chosen.size > 1:
+        a, b = rng.choice(chosen, 2, replace=False)
+        s[a], s[b] = s[b], s[a]
+    return s
+
+
+@pytest.mark.parametrize("eps", [0, 10000, 250000, 1000000])
+def test_fast_certificate_agrees_with_the_replay(gg, orc, eps):
+    """The O(n + m) certificate and the step-by-step replay check the same properties:
+    both accept the oracle's covers, and they agree on every perturbed answer."""
+    rng = np.random.default_rng(eps)
+    rejected = 0
+    for seed in range(12):
+        g = _random_sym(gg, 30 + 5 * seed, 0.05 + 0.02 * (seed % 5), 100 + seed)
+        pri = np.random.default_rng(seed).permutation(g.n)
+        s, k = orc.setcover(g, pri, eps)
+        assert orc.check_setcover(g, s, k, eps) == (0, 0)
+        assert certify(g, s, k, eps) == []
+        for _ in range(15):
+            t = _perturb(s, rng)
+            fast = orc.check_setcover(g, t, k, eps)[0] == 0
+            slow = certify(g, t, k, eps) == []
+            assert fast == slow, (seed, t.tolist())
+            rejected += not fast
+    assert rejected > 30
+
+
+def test_fast_certificate_codes(gg, orc):
+    g = _sym_simple(gg, 6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5)])
+    s, k = orc.setcover(g, np.arange(6), 10000)
+    assert orc.check_setcover(g, s, k) == (0, 0)
+    t = s.copy()
+    t[:] = 0
+    assert orc.check_setcover(g, t, k)[0] == 1        # nothing chosen: not a cover
+    t = s.copy()
+    t[0] = k + 1
+    assert orc.check_setcover(g, t, k) == (4, 0)      # a step beyond the run
+    star = _sym_simple(gg, 8, [(0, i) for i in range(1, 8)])
+    s, k = orc.setcover(star, np.arange(8), 10000)
+    t = s.copy()
+    t[1:] = 1                                         # every leaf joins with the centre
+    assert orc.check_setcover(star, t, k)[0] in (2, 3)
