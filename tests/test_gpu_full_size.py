@@ -19,7 +19,8 @@
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
+# generous limits (pytest-timeout): graph generation and the one-core oracle dominate
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(900)]
 
 
 @pytest.fixture(scope="module")
