@@ -489,14 +489,31 @@ __device__ void phase_c(const ScParams& P, const ScSmem& S, ScCnt& C) {
   large_settle(P, S, C);
 }
 
-// Run by warp 0 of the CTA that arrives last at a grid barrier: the next phase.
+// Warp-uniform reads for the decider: lane 0 reads, every lane takes its value.  The
+// decider's lane 0 also rewrites some of these words, and the lanes of a warp are not
+// guaranteed to run in lockstep, so a lane reading a word itself could see lane 0's new
+// value while the others saw the old one, decide differently and leave the others
+// waiting in a collective.
+__device__ __forceinline__ uint32_t uread(const uint32_t* p) {
+  uint32_t v = 0;
+  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
+  return __shfl_sync(FULL, v, 0);
+}
+__device__ __forceinline__ unsigned long long uread64(const unsigned long long* p) {
+  unsigned long long v = 0;
+  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
+  return __shfl_sync(FULL, v, 0);
+}
+
+// Run by warp 0 of the CTA that arrives last at a grid barrier: the next phase.  Every
+// value a decision depends on is read warp-uniformly (uread).
 __device__ void sc_decide(const ScParams& P, uint32_t done) {
   const uint32_t lane = threadIdx.x & 31;
   ScState* ss = P.ss;
-  const bool fatal = (ld_relaxed(&P.sync->err) & kErrFatal) != 0u;
+  const bool fatal = (uread(&P.sync->err) & kErrFatal) != 0u;
   uint32_t next = kScStop;
   auto large_n = [&](uint32_t sel) -> uint32_t {
-    return (uint32_t)(__ldcg(&ss->bw[sel]) >> kScCntShift);
+    return (uint32_t)(uread64(&ss->bw[sel]) >> kScCntShift);
   };
   // The highest non-empty band at or below `from`; its largest bucket is gathered next.
   auto transition = [&](int from) -> uint32_t {
@@ -523,7 +540,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
   // A step either adds a set to the cover or empties its bucket (every member leaves or
   // moves down), so a run takes at most n + nb steps; more means a broken invariant.
   auto start_step = [&]() -> uint32_t {
-    const uint32_t s = __ldcg(&ss->step) + 1u;
+    const uint32_t s = uread(&ss->step) + 1u;
     if ((unsigned long long)s > (unsigned long long)P.n + P.nb + 1ull) {
       if (lane == 0) report_bad(P.sync, 63u, s, __ldcg(&ss->j));
       return kScStop;
@@ -535,19 +552,19 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
     return kScA;
   };
   if (!fatal) {
-    const uint32_t c = __ldcg(&ss->csel);
+    const uint32_t c = uread(&ss->csel) & 1u;
     switch (done) {
       case kScPrologue:
         next = transition((int)P.nbands - 1);
         break;
       case kScGather: {
-        const uint32_t b = __ldcg(&ss->band);
+        const uint32_t b = uread(&ss->band);
         if (lane == 0) {
           P.bsel[b] = __ldcg(P.bsel + b) ^ 1u;
           P.bcnt[b] = __ldcg(&ss->gcnt);
           P.bmax[b] = __ldcg(&ss->gmax);
         }
-        if (__ldcg(&ss->ns[c]) + large_n(c) == 0u) {
+        if (uread(&ss->ns[c]) + large_n(c) == 0u) {
           if (lane == 0) report_bad(P.sync, 54u, __ldcg(&ss->j), b);
           next = kScStop;
         } else {
@@ -568,7 +585,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
           break;
         }
         const uint32_t x = c ^ 1u;
-        if (__ldcg(&ss->ns[x]) + large_n(x) > 0u) {
+        if (uread(&ss->ns[x]) + large_n(x) > 0u) {
           if (lane == 0) {
             ss->csel = x;
             ss->ns[c] = 0u;
@@ -576,7 +593,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
           }
           next = start_step();
         } else {
-          next = transition((int)__ldcg(&ss->band));
+          next = transition((int)uread(&ss->band));
         }
         break;
       }
