@@ -382,12 +382,29 @@ __device__ void scan_phase(const KParams& P, KSmem& S) {
   }
 }
 
+// Warp-uniform reads for the decider: lane 0 reads, every lane takes its value.  Lane 0
+// of the deciding warp also rewrites some of these words, and the lanes of a warp are not
+// guaranteed to run in lockstep, so a lane reading a word itself could see the new value
+// while the others saw the old one, decide differently and leave the others waiting in
+// a collective.
+__device__ __forceinline__ uint32_t kread(const uint32_t* p) {
+  uint32_t v = 0;
+  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
+  return __shfl_sync(FULL, v, 0);
+}
+__device__ __forceinline__ unsigned long long kread64(const unsigned long long* p) {
+  unsigned long long v = 0;
+  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
+  return __shfl_sync(FULL, v, 0);
+}
+
 // Run by warp 0 of the CTA that arrives last at a grid barrier: the next phase and level.
+// Every value a decision depends on is read warp-uniformly (kread).
 __device__ void kdecide(const KParams& P, uint32_t done) {
   const uint32_t lane = threadIdx.x & 31;
   KState* ks = P.ks;
   Sync* sy = P.sync;
-  const bool fatal = (ld_relaxed(&sy->err) & kErrFatal) != 0u;
+  const bool fatal = (kread(&sy->err) & kErrFatal) != 0u;
   uint32_t next = kKStop;
   // Level c of the window: a bucket that overflowed is rebuilt by a scan.
   // The state words were written by earlier deciders on other SMs: read them from L2.
@@ -397,7 +414,7 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
       ks->k = __ldcg(&ks->base) + c;
       ks->levels = __ldcg(&ks->levels) + 1u;
     }
-    if (__ldcg(P.lossy + c)) {
+    if (kread(P.lossy + c)) {
       if (lane == 0) {
         ks->next_n[__ldcg(&ks->asel)] = 0u;
         ks->scans = __ldcg(&ks->scans) + 1u;
@@ -413,7 +430,7 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
   // The level is done: the next non-empty (or overflowed) bucket of the window, else a
   // refill of the window from the smallest priority above it.
   auto level_done = [&]() -> uint32_t {
-    const uint32_t cur = __ldcg(&ks->cur);
+    const uint32_t cur = kread(&ks->cur);
     for (uint32_t c0 = cur + 1; c0 < kKRing; c0 += 32) {
       const uint32_t c = c0 + lane;
       const bool ne = c < kKRing && (__ldcg(P.counts + c) > 0u || __ldcg(P.lossy + c) != 0u);
@@ -430,8 +447,8 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
   // Eager: vertices that dropped to k wait in list[asel]; they are the next round.
   auto after_round = [&]() -> uint32_t {
     if (lane == 0) P.stats->v[kStRounds] += 1ull;
-    const uint32_t a = __ldcg(&ks->asel);
-    const uint32_t na = __ldcg(&ks->next_n[a]);
+    const uint32_t a = kread(&ks->asel);
+    const uint32_t na = kread(&ks->next_n[a]);
     if (na > 0u) {  // vertices dropped to k: another round at this level
       if (lane == 0) {
         ks->fr_list = 1u;
@@ -448,8 +465,8 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
   // extracted) by the next apply phase, which counts into the other list, reset here.
   auto lazy_next = [&]() -> uint32_t {
     if (lane == 0) P.stats->v[kStRounds] += 1ull;
-    const uint32_t t = __ldcg(&ks->tsel);
-    if (__ldcg(&ks->touched_n[t]) > 0u) {
+    const uint32_t t = kread(&ks->tsel);
+    if (kread(&ks->touched_n[t]) > 0u) {
       if (lane == 0) {
         ks->tsel = t ^ 1u;
         ks->touched_n[t ^ 1u] = 0u;
@@ -468,7 +485,7 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
         next = kKMin;
         break;
       case kKMin: {
-        const uint32_t km = __ldcg(&ks->kmin);
+        const uint32_t km = kread(&ks->kmin);
         if (km == kInf) {
           next = kKStop;
         } else {
@@ -497,7 +514,7 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
         break;
       case kKPeel:
       case kKApply:
-        if ((__ldcg(&ks->hub_word) >> 32) > 0u) {  // hubs listed: their edges first
+        if ((kread64(&ks->hub_word) >> 32) > 0u) {  // hubs listed: their edges first
           next = kKHub;
           break;
         }
