@@ -58,3 +58,28 @@ def test_reference_metrics_name_every_workload():
                "road-lazy", "rmat-lazy", "rmat-kcore", "rmat-setcover"}
     assert set(bench.REF_METRIC) == choices
     assert "queries/s" in bench.REF_METRIC["batch"] and "GTEPS" in bench.REF_METRIC["road-sssp"]
+
+
+def test_reference_arm_prints_one_contract_line_on_rank_zero(monkeypatch, capsys):
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    bench.run_reference(bench.parse_args(["--impl", "reference", "--side", "48",
+                                          "--sources", "2", "--steps", "3", "--warmup", "1"]))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.REF_METRIC["road-sssp"]
+    assert d["unit"] == "GTEPS" and d["value"] > 0 and d["higher_is_better"] is True
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (3, 1, 1)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.run_reference(bench.parse_args(["--impl", "reference", "--side", "48"]))
+    assert capsys.readouterr().out == ""
