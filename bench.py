@@ -146,12 +146,9 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self) -> dict:
-        rows = []
+        lines = []
         try:
-            for line in open(self.path):
-                f = [x.strip() for x in line.split(",")]
-                if len(f) >= 9 and f[1].isdigit():
-                    rows.append(f)
+            lines = open(self.path).read().splitlines()
         except OSError:
             pass
         finally:
@@ -159,16 +156,28 @@ class ClockSampler:
                 os.unlink(self.path)
             except OSError:
                 pass
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [int(r[1]) for r in rows]
-        mx = max(int(r[2]) for r in rows)
-        loaded = [s for s, r in zip(sm, rows) if float(r[3] or 0) > 200.0] or sm
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
-        return {"sm_mhz": int(statistics.median(loaded)), "sm_max_mhz": mx,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3] or 0) for r in rows)}
+        return clock_summary(lines)
+
+
+def clock_summary(lines) -> dict:
+    """Summary of nvidia-smi samples (SMI_FIELDS, csv, noheader, nounits): the median SM
+    clock over the samples drawing more than 200 W (all samples when none does), the
+    highest max clock, and every throttle reason seen Active."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) >= 9 and f[1].isdigit():
+            rows.append(f)
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+    sm = [int(r[1]) for r in rows]
+    mx = max(int(r[2]) for r in rows)
+    loaded = [s for s, r in zip(sm, rows) if float(r[3] or 0) > 200.0] or sm
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+    return {"sm_mhz": int(statistics.median(loaded)), "sm_max_mhz": mx,
+            "reasons": reasons, "samples": len(rows),
+            "power_w_max": max(float(r[3] or 0) for r in rows)}
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of og_delta_kernel from one

@@ -83,3 +83,24 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(bench.parse_args(["--impl", "reference", "--side", "48"]))
     assert capsys.readouterr().out == ""
+
+
+def test_clock_summary_takes_loaded_samples_and_active_reasons():
+    na = "Not Active"
+    rows = [
+        f"0, 1980, 2070, 150.2, 0x0000000000000000, {na}, {na}, {na}, {na}",  # idle
+        f"0, 2070, 2070, 910.5, 0x0000000000000000, {na}, {na}, {na}, {na}",
+        f"0, 2055, 2070, 1390.0, 0x0000000000000004, {na}, {na}, {na}, Active",
+        f"0, 2040, 2070, 1201.7, 0x0000000000000004, {na}, {na}, {na}, Active",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",  # unreadable sample
+        "",
+    ]
+    s = bench.clock_summary(rows)
+    assert s["samples"] == 4 and s["sm_max_mhz"] == 2070
+    assert s["sm_mhz"] == 2055  # median of the three samples above 200 W
+    assert s["reasons"] == ["sw_power_cap"] and s["power_w_max"] == 1390.0
+    slow = rows[1].replace(f"{na}, {na}, {na}, {na}", f"Active, {na}, Active, {na}")
+    assert bench.clock_summary([slow])["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    # no load at all: the median of every sample; nothing parsed: marked unsampled
+    assert bench.clock_summary(rows[:1])["sm_mhz"] == 1980
+    assert bench.clock_summary([])["reasons"] == ["unsampled"]
