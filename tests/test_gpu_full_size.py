@@ -12,6 +12,9 @@
 * R-MAT scale 24 (16,777,216 vertices, 520,762,674 directed edges, weights in
   [1, 2^16)) with the bench's 8 sources and its tuned schedule (Delta 256, fusion off,
   tile 256): the certificate on two sources (a Dijkstra there takes ~40 s a source).
+* R-MAT scale 24 wBFS (the same structure with weights in [1, 24)), the bench's 8
+  sources in one launch under the library's default schedule (Delta 1): every source's
+  distances pass the certificate, and one is compared element by element with Dijkstra.
 * Set cover on the same R-MAT graph (its structure does not depend on the weight range,
   and set cover ignores weights, so it is the `rmat-setcover` workload), in the bench's
   launch shape and another one: every set's join step equals the oracle's.
@@ -77,6 +80,24 @@ def test_full_size_rmat_sssp_batch_certified(og, orc, rmat24):
         assert orc.check_sssp(g, int(srcs[i]), d[i]) == (0, 0), i
     del out
     G.free()
+
+
+def test_full_size_rmat_wbfs_batch_vs_oracle(og, orc):
+    import torch
+    import bench
+    g, _, srcs = bench.build_workload(bench.parse_args(["--workload", "rmat-wbfs"]), 0, 1)
+    assert (g.n, g.m, len(srcs)) == (16777216, 520762674, 8)
+    assert int(g.w.min()) >= 1 and int(g.w.max()) < 24
+    G = og.Graph.from_csr(g)
+    queries = [(og.Q_WBFS, int(s), 0, 0) for s in srcs]
+    out = torch.empty(len(queries) * g.n, dtype=torch.int32, device="cuda")
+    og.batch_run(G, queries, out=out)
+    d = out.cpu().numpy().view(np.uint32).reshape(len(queries), g.n)
+    del out
+    G.free()
+    for i, s in enumerate(srcs):
+        assert orc.check_sssp(g, int(s), d[i]) == (0, 0), i
+    np.testing.assert_array_equal(d[0], orc.dijkstra(g, int(srcs[0])))
 
 
 def test_full_size_rmat_setcover(og, orc, gg, rmat24):
