@@ -59,6 +59,8 @@ def _load():
         L.or_kcore.argtypes = [u32, vp, vp, vp]
         L.or_setcover.restype = ctypes.c_int
         L.or_setcover.argtypes = [u32, vp, vp, u32, vp, vp, vp]
+        L.or_check_kcore.restype = ctypes.c_int
+        L.or_check_kcore.argtypes = [u32, vp, vp, vp, vp]
         L.or_check_setcover.restype = ctypes.c_int
         L.or_check_setcover.argtypes = [u32, vp, vp, u32, vp, ctypes.c_uint64, vp]
         _lib = L
@@ -135,6 +137,22 @@ def kcore(g) -> np.ndarray:
     out = np.empty(g.n, np.uint32)
     _status(_load().or_kcore(g.n, off.ctypes.data, nbr.ctypes.data, out.ctypes.data), False)
     return out
+
+
+def check_kcore(g, core) -> tuple[int, int]:
+    """Certificate of a coreness vector (``oracle.c``, ``or_check_kcore``), O(n + m).
+    Returns (code, vertex): 0 = what ``kcore`` computes; 1 = a vertex keeps fewer than
+    core[v] entries from vertices of core >= core[v] (its value is too high); 2 = a
+    vertex of some level cannot be extracted at that level (a value too low somewhere)."""
+    off, nbr, _ = _csr(g)
+    c = np.ascontiguousarray(core, dtype=np.uint32)
+    if c.shape != (g.n,):
+        raise OracleError("one coreness per vertex")
+    bad = ctypes.c_uint32(0)
+    code = _load().or_check_kcore(g.n, off.ctypes.data, nbr.ctypes.data, c.ctypes.data,
+                                  ctypes.byref(bad))
+    _status(code if code < 0 else 0, False)
+    return int(code), int(bad.value)
 
 
 def setcover(g, pri, eps_ppm: int = 10000) -> tuple[np.ndarray, int]:

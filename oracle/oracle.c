@@ -31,6 +31,18 @@
  *                       entries, so on a symmetric simple graph this is the usual
  *                       coreness; the minimum is taken with the binary heap above
  *                       (stale heap entries are skipped).
+ *   - or_check_kcore:   certificate of a coreness vector c for or_kcore's peeling, in
+ *                       O(n + m) (the heap makes or_kcore O(m log n)): (a) every v keeps
+ *                       at least c(v) entries once every entry w -> v with c(w) < c(v)
+ *                       is taken away, so no level below c(v) can extract v; (b) taking
+ *                       the levels k in ascending order, after every vertex with
+ *                       c < k is gone, repeatedly extracting a vertex with c = k that
+ *                       has at most k entries left removes every vertex with c = k.
+ *                       (a) and (b) hold together for or_kcore's output only: (b) makes
+ *                       each level's closure take all of {c = k}, (a) keeps it from
+ *                       taking anything else.  On a symmetric graph (a) reads "v has at
+ *                       least c(v) neighbours u with c(u) >= c(v)", the definition of the
+ *                       c(v)-core, and (b) shows v outside the (c(v) + 1)-core.
  *   - or_setcover:      approximate unweighted set cover (Section 6.1, "Approximate Set
  *                       Cover"), the graph read as a set system: the set of vertex v is
  *                       its adjacency list S_v (entries counted with multiplicity), the
@@ -277,6 +289,107 @@ int or_kcore(uint32_t n, const uint64_t *off, const uint32_t *nbr, uint32_t *cor
   free(done);
   free(h);
   return OR_OK;
+}
+
+/* Certificate of a coreness vector (see the header): returns 0 when core[] is what
+ * or_kcore computes, 1 when (a) fails at vertex *bad, 2 when (b) fails (*bad = a vertex
+ * of the level that could not be extracted), OR_INVALID / OR_NOMEM otherwise. */
+int or_check_kcore(uint32_t n, const uint64_t *off, const uint32_t *nbr, const uint32_t *core,
+                   uint32_t *bad) {
+  if (n == 0 || !core || !bad) return OR_INVALID;
+  *bad = 0;
+  const uint64_t m = off[n];
+  for (uint64_t e = 0; e < m; ++e)
+    if (nbr[e] >= n) return OR_INVALID;
+  /* (a): entries w -> v with core[w] < core[v] (on a directed graph they may outnumber
+   * v's own entries, so they are counted, not subtracted) */
+  uint64_t *left = (uint64_t *)calloc(n, sizeof(uint64_t));
+  if (!left) return OR_NOMEM;
+  for (uint32_t w = 0; w < n; ++w)
+    for (uint64_t e = off[w]; e < off[w + 1]; ++e)
+      if (core[w] < core[nbr[e]]) left[nbr[e]] += 1;
+  for (uint32_t v = 0; v < n; ++v) {
+    if ((uint64_t)core[v] + left[v] > off[v + 1] - off[v]) {
+      *bad = v;
+      free(left);
+      return 1;
+    }
+  }
+  /* (b): levels in ascending order (vertices sorted by core[] with a counting sort; (a)
+   * bounds every core[v] by v's degree, so the levels fit in m + 1 counters) */
+  uint32_t maxc = 0;
+  for (uint32_t v = 0; v < n; ++v)
+    if (core[v] > maxc) maxc = core[v];
+  uint64_t *start = (uint64_t *)calloc((size_t)maxc + 2, sizeof(uint64_t));
+  uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * n);
+  unsigned char *state = (unsigned char *)calloc(n, 1); /* 1 queued, 2 extracted */
+  if (!start || !order || !queue || !state) {
+    free(left);
+    free(start);
+    free(order);
+    free(queue);
+    free(state);
+    return OR_NOMEM;
+  }
+  for (uint32_t v = 0; v < n; ++v) start[core[v] + 1] += 1;
+  for (uint32_t k = 0; k <= maxc; ++k) start[k + 1] += start[k];
+  {
+    uint64_t *fill = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)maxc + 1));
+    if (!fill) {
+      free(left);
+      free(start);
+      free(order);
+      free(queue);
+      free(state);
+      return OR_NOMEM;
+    }
+    memcpy(fill, start, sizeof(uint64_t) * ((size_t)maxc + 1));
+    for (uint32_t v = 0; v < n; ++v) order[fill[core[v]]++] = v;
+    free(fill);
+  }
+  /* entries left to each vertex while the levels are extracted, floored at 0 (the
+   * peeling floors a priority at the level, and "left <= k" is the same test) */
+  for (uint32_t v = 0; v < n; ++v) left[v] = off[v + 1] - off[v];
+  int code = 0;
+  for (uint32_t k = 0; k <= maxc && code == 0; ++k) {
+    uint64_t qh = 0, qt = 0;
+    for (uint64_t i = start[k]; i < start[k + 1]; ++i) {
+      const uint32_t v = order[i];
+      if (left[v] <= k) {
+        state[v] = 1;
+        queue[qt++] = v;
+      }
+    }
+    while (qh < qt) {
+      const uint32_t v = queue[qh++];
+      state[v] = 2;
+      for (uint64_t e = off[v]; e < off[v + 1]; ++e) {
+        const uint32_t u = nbr[e];
+        if (state[u] == 2) continue;
+        if (left[u] > 0) left[u] -= 1;
+        if (core[u] == k && state[u] == 0 && left[u] <= k) {
+          state[u] = 1;
+          queue[qt++] = u;
+        }
+      }
+    }
+    if (qt != start[k + 1] - start[k]) {
+      for (uint64_t i = start[k]; i < start[k + 1]; ++i) {
+        if (state[order[i]] != 2) {
+          *bad = order[i];
+          break;
+        }
+      }
+      code = 2;
+    }
+  }
+  free(left);
+  free(start);
+  free(order);
+  free(queue);
+  free(state);
+  return code;
 }
 
 /* Bucket of a residual size d >= 1 on the ladder t[0 .. nb] (t[nb] > every size):

@@ -15,6 +15,11 @@
 * R-MAT scale 24 wBFS (the same structure with weights in [1, 24)), the bench's 8
   sources in one launch under the library's default schedule (Delta 1): every source's
   distances pass the certificate, and one is compared element by element with Dijkstra.
+* k-core on the same R-MAT graph (the bench's `rmat-kcore` graph: the generator's
+  structure does not depend on the weight range, and k-core ignores weights), lazy and
+  eager in the bench's launch: the lazy result passes the oracle's linear-time k-core
+  certificate, which only the exact coreness passes (the oracle's own peeling takes ~5
+  minutes at this size), and the eager result equals it.
 * Set cover on the same R-MAT graph (its structure does not depend on the weight range,
   and set cover ignores weights, so it is the `rmat-setcover` workload), in the bench's
   launch shape and another one: every set's join step equals the oracle's.
@@ -98,6 +103,22 @@ def test_full_size_rmat_wbfs_batch_vs_oracle(og, orc):
     for i, s in enumerate(srcs):
         assert orc.check_sssp(g, int(s), d[i]) == (0, 0), i
     np.testing.assert_array_equal(d[0], orc.dijkstra(g, int(srcs[0])))
+
+
+def test_full_size_rmat_kcore_certified(og, orc, rmat24):
+    import torch
+    g, _ = rmat24
+    G = og.Graph.from_csr(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    og.kcore(G, og.KCORE_LAZY, out=out)
+    lazy = out.cpu().numpy().view(np.uint32).copy()
+    og.kcore(G, og.KCORE_EAGER, out=out)
+    eager = out.cpu().numpy().view(np.uint32).copy()
+    del out
+    G.free()
+    assert int(lazy.max()) == 1621
+    assert orc.check_kcore(g, lazy) == (0, 0)
+    np.testing.assert_array_equal(eager, lazy)
 
 
 def test_full_size_rmat_setcover(og, orc, gg, rmat24):

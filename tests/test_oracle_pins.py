@@ -284,6 +284,73 @@ def test_kcore_level_sets_are_cores(gg, orc):
         assert (cnt[core == k] <= k).all()
 
 
+def _kcore_graphs(gg):
+    """Symmetric, multigraph, directed and self-loop cases for the k-core certificate."""
+    out = [("clique9", _sym(gg, 9, list(itertools.combinations(range(9), 2)))),
+           ("path+isolated", _sym(gg, 8, [(i, i + 1) for i in range(6)])),
+           ("K4,7", _sym(gg, 11, [(i, 4 + j) for i in range(4) for j in range(7)])),
+           ("grid", gg.grid(9, 11, 1, 9, seed=3)),
+           ("rmat9", gg.rmat(9, 8, 0.57, 0.19, 0.19, 1, 2, seed=2)),
+           ("multigraph", gg.from_edges(3, [0, 0, 0, 1, 1, 1, 1, 2], [1, 1, 1, 0, 0, 0, 2, 1],
+                                        [1] * 8))]
+    rng = np.random.default_rng(7)
+    for i in range(4):
+        n = 40 + 10 * i
+        s = rng.integers(0, n, 4 * n)
+        d = rng.integers(0, n, 4 * n)  # directed, with self-loops and parallel entries
+        out.append((f"directed{i}", gg.from_edges(n, s, d, np.ones(len(s), np.uint32))))
+    return out
+
+
+def test_kcore_certificate_accepts_the_oracle_and_nothing_else(gg, orc):
+    """The certificate holds for or_kcore's output on every graph kind, and fails for
+    every vector that differs from it in one vertex by +1 or -1 (the coreness vector is
+    the only one that passes)."""
+    for name, g in _kcore_graphs(gg):
+        core = orc.kcore(g)
+        assert orc.check_kcore(g, core) == (0, 0), name
+        for v in range(g.n):
+            for dv in (1, -1):
+                if core[v] == 0 and dv < 0:
+                    continue
+                c = core.astype(np.int64)
+                c[v] += dv
+                assert orc.check_kcore(g, c.astype(np.uint32))[0] in (1, 2), (name, v, dv)
+
+
+def test_kcore_certificate_codes(gg, orc):
+    """A value above the vertex's degree fails (a) at that vertex; all zeros on a graph
+    with an edge fails (b) at level 0; degrees fail unless every vertex is extracted at
+    its own degree (a cycle: degree 2 = coreness 2)."""
+    g = _sym(gg, 8, [(i, i + 1) for i in range(6)])  # path on 0..6, vertex 7 isolated
+    c = orc.kcore(g).copy()
+    c[3] = 3
+    assert orc.check_kcore(g, c) == (1, 3)
+    code, v = orc.check_kcore(g, np.zeros(g.n, np.uint32))
+    assert code == 2 and 0 <= v < 7
+    deg = np.diff(g.offsets).astype(np.uint32)
+    assert orc.check_kcore(g, deg)[0] == 1
+    cyc = _sym(gg, 12, [(i, (i + 1) % 12) for i in range(12)])
+    assert orc.check_kcore(cyc, np.diff(cyc.offsets).astype(np.uint32)) == (0, 0)
+    with pytest.raises(orc.OracleError):
+        orc.check_kcore(g, np.zeros(g.n - 1, np.uint32))
+
+
+def test_kcore_certificate_on_random_perturbations(gg, orc):
+    """R-MAT scale 12: 300 vectors with a few random changes each are all rejected."""
+    g = gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 2, seed=4)
+    core = orc.kcore(g)
+    assert orc.check_kcore(g, core) == (0, 0)
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        c = core.astype(np.int64)
+        idx = rng.integers(0, g.n, rng.integers(1, 4))
+        c[idx] = np.maximum(0, c[idx] + rng.choice([-2, -1, 1, 2], len(idx)))
+        if (c == core).all():
+            continue
+        assert orc.check_kcore(g, c.astype(np.uint32))[0] in (1, 2)
+
+
 # ---- k-core mutants: plausible mistakes planted in a copy of the oracle's source ---------
 
 # The floor at the level k and the level that only rises each keep the result exact on
