@@ -811,6 +811,11 @@ def run_kcore(args):
                "kind": "oracle",
                "sample": f"the oracle's peeling (binary heap) on R-MAT scale 20 from the same "
                          f"generator ({small.n} V, {small.m} E), {dt:.1f} s"}
+    # the full-size result against the oracle's linear-time k-core certificate (only the
+    # exact coreness passes it; the oracle's own peeling takes minutes at scale 24)
+    certified = None
+    if not args.no_cpu_baseline:
+        certified = oracle.check_kcore(g, ref_core) == (0, 0)
     line = {
         "metric": "k-core GTEPS (directed edges / time, lazy bucket update with histogram)",
         "value": round(g.m / step_s / 1e9, 4), "unit": "GTEPS", "n_gpus": 1,
@@ -841,6 +846,7 @@ def run_kcore(args):
                  "priority_updates": int(st.improved), "bucket_inserts": int(st.global_inserts),
                  "window_refills": int(st.redistributions), "scanned_levels": int(st.flushes)},
         "exact_lazy_eq_eager_eq_host": same,
+        "exact_vs_oracle_certificate": certified,
         "cpu_baseline": cpu,
         "e2e": {"value": round(g.m / e2e_s / 1e9, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * g.n, "ms_per_step": round(e2e_s * 1e3, 3)},
