@@ -3,8 +3,9 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this package.  It computes the plain definition of shortest-path distances
 (``oracle.c``: Dijkstra, BFS, Bellman-Ford, certificate check) and
-k-core coreness by peeling, approximate set cover by bucketed nearly independent
-steps and a certificate for set covers, and shares no code with
+k-core coreness by peeling and a linear-time certificate of coreness, approximate set
+cover by bucketed nearly independent steps and a certificate for set covers, and shares
+no code with
 the CUDA path in ``paper_1911_07260_gb300``.
 
 Each wrapper takes a ``graphgen.Graph`` (CSR: uint64 offsets, uint32 neighbours,
