@@ -302,6 +302,34 @@ def _kcore_graphs(gg):
     return out
 
 
+@pytest.mark.parametrize("case", range(6))
+def test_kcore_vs_networkx_core_number(gg, orc, case):
+    """On simple undirected graphs the peeling's coreness equals networkx's core_number
+    (an independent implementation of the textbook definition): random graphs from
+    sparse to dense, and cleaned symmetric R-MAT graphs with their skewed degrees."""
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(100 + case)
+    if case < 4:
+        n = 300 + 150 * case
+        m = int(n * (2 + 6 * case))
+        a, b = rng.integers(0, n, m), rng.integers(0, n, m)
+        keep = a != b
+        pairs = {(int(min(x, y)), int(max(x, y))) for x, y in zip(a[keep], b[keep])}
+        g = _sym(gg, n, sorted(pairs))
+    else:
+        g = gg.rmat(9 + case, 16, 0.57, 0.19, 0.19, 1, 2, seed=case)
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets.astype(np.int64)))
+    assert not (src == g.nbr).any()  # simple: no self-loops
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_edges_from(zip(src.tolist(), g.nbr.tolist()))
+    assert 2 * G.number_of_edges() == g.m  # symmetric, no parallel entries
+    want = nx.core_number(G)
+    got = orc.kcore(g)
+    assert got.tolist() == [want[v] for v in range(g.n)]
+    assert orc.check_kcore(g, got) == (0, 0)
+
+
 def test_kcore_certificate_accepts_the_oracle_and_nothing_else(gg, orc):
     """The certificate holds for or_kcore's output on every graph kind, and fails for
     every vector that differs from it in one vertex by +1 or -1 (the coreness vector is
