@@ -96,3 +96,24 @@ def test_grid_step_pairs(gg):
     assert l1.min() >= 10 and l1.max() <= 100
     src = gg.sample_sources(g, 8, seed=2)
     assert src.dtype == np.uint32 and len(set(src.tolist())) == 8
+
+
+def test_priorities_are_seeded_permutations(gg):
+    for n in (1, 7, 1000):
+        p = gg.priorities(n, seed=5)
+        assert p.dtype == np.uint32 and sorted(p.tolist()) == list(range(n))
+        np.testing.assert_array_equal(p, gg.priorities(n, seed=5))
+    assert not np.array_equal(gg.priorities(1000, seed=5), gg.priorities(1000, seed=6))
+
+
+def test_rmat_structure_does_not_depend_on_the_weight_range(gg):
+    """The full-size k-core and set cover tests take the R-MAT SSSP graph for the bench's
+    k-core / set cover graph (same generator and seed, weights in [1, 2)): the two share
+    offsets and neighbours, only the weights differ."""
+    a = gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
+    b = gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 1 << 16, seed=1)
+    c = gg.rmat(13, 16, 0.57, 0.19, 0.19, 1, 24, seed=1)
+    for x in (b, c):
+        np.testing.assert_array_equal(a.offsets, x.offsets)
+        np.testing.assert_array_equal(a.nbr, x.nbr)
+    assert int(a.w.max()) == 1 and int(b.w.max()) > 24 and int(c.w.max()) < 24
