@@ -346,6 +346,25 @@ def test_kcore_certificate_accepts_the_oracle_and_nothing_else(gg, orc):
                 assert orc.check_kcore(g, c.astype(np.uint32))[0] in (1, 2), (name, v, dv)
 
 
+@pytest.mark.parametrize("seed", range(20))
+def test_kcore_certificate_on_random_directed_multigraphs(gg, orc, seed):
+    """Directed graphs with self-loops and parallel entries, from very sparse to dense:
+    the oracle's peeling passes, and 50 random changes of one to three values fail."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(5, 120))
+    m = int(rng.integers(0, 12 * n))
+    g = gg.from_edges(n, rng.integers(0, n, m), rng.integers(0, n, m), np.ones(m, np.uint32))
+    core = orc.kcore(g)
+    assert orc.check_kcore(g, core) == (0, 0)
+    for _ in range(50):
+        c = core.astype(np.int64)
+        idx = rng.integers(0, n, rng.integers(1, 4))
+        c[idx] = np.maximum(0, c[idx] + rng.choice([-1, 1], len(idx)))
+        if (c == core).all():
+            continue
+        assert orc.check_kcore(g, c.astype(np.uint32))[0] in (1, 2)
+
+
 def test_kcore_certificate_codes(gg, orc):
     """A value above the vertex's degree fails (a) at that vertex; all zeros on a graph
     with an edge fails (b) at level 0; degrees fail unless every vertex is extracted at
