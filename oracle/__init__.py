@@ -143,8 +143,10 @@ def kcore(g) -> np.ndarray:
 def check_kcore(g, core) -> tuple[int, int]:
     """Certificate of a coreness vector (``oracle.c``, ``or_check_kcore``), O(n + m).
     Returns (code, vertex): 0 = what ``kcore`` computes; 1 = a vertex keeps fewer than
-    core[v] entries from vertices of core >= core[v] (its value is too high); 2 = a
-    vertex of some level cannot be extracted at that level (a value too low somewhere)."""
+    core[v] of its entries once every entry w -> v with core[w] < core[v] is taken away
+    (its value is too high; on a symmetric graph: fewer than core[v] neighbours of value
+    >= core[v]); 2 = a vertex of some level cannot be extracted at that level (a value
+    too low somewhere)."""
     off, nbr, _ = _csr(g)
     c = np.ascontiguousarray(core, dtype=np.uint32)
     if c.shape != (g.n,):
