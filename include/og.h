@@ -342,20 +342,45 @@ int og_autotune_batch(og_graph* g, const og_query* queries, uint32_t nq, uint32_
  *   pairs, the out-edges of u at pairs offsets[u] .. offsets[u+1]-1; dist_out: device
  *   uint32[n], receives every distance from src (0xFFFFFFFF = unreachable).  All three
  *   stay owned by the caller.
+ *   The graph is checked on the device before the search: offsets[0] = 0,
+ *   offsets[n] = m, offsets non-decreasing and every neighbor < n, else OG_E_INVALID
+ *   (the search never runs on a malformed graph; the check reads offsets[0 .. n] and the
+ *   m pairs only).  OG_E_INTERNAL reports a failed internal bounds check of the kernel
+ *   (og_last_cuda_error has the details), OG_E_TIMEOUT a grid-barrier wait that gave up.
  *   Scratch: a 64 MiB static device array inside libog.so, reserved on every GPU that
  *   loads the library until the process exits.  n above 2^20 (1,048,576) vertices is
  *   rejected with OG_E_INVALID; a run whose buckets outgrow the array returns OG_E_ARENA
  *   (it never grows).
- *   The first call on a device looks up the array's device address (set-up, once per
- *   device); make that first call before any stream capture.  Every call shares the
- *   array and clears its state words first, so calls that overlap on the GPU (other
- *   streams, other host threads) race: serialise them.  Synchronises stream before
- *   returning, like og_sssp_delta. */
+ *   The first call on a device, and the first after the device's context was re-created
+ *   (cudaDeviceReset), does the set-up: it looks up the array's device address.  Make
+ *   that first call before any stream capture.  Every call shares the array and clears
+ *   its state words first, so calls that overlap on the GPU (other streams, other host
+ *   threads) race: serialise them.  The call synchronises stream twice (after the graph
+ *   check and at the end) before returning its status. */
 int og_sssp_delta_noalloc(const uint32_t* offsets, const uint32_t* edges, uint32_t n,
                           uint64_t m, uint32_t src, uint32_t delta, uint32_t* dist_out,
                           void* stream);
 
 /* ---- diagnostics ----------------------------------------------------------------------- */
+/* The status every round-engine entry point derives from the error word its persistent
+ * launch leaves behind (exposed so that the mapping can be checked without a GPU):
+ * err = the launch's error bits (1 a bounded wait gave up, 2 a query's arena ran out, 4 a
+ * distance saturated, 8 an internal bounds check failed); bad_code / bad_val / bad_aux =
+ * the first failed check's code, value and context; arena_out = a query ran out of
+ * bucket space where the arena cannot grow.  Precedence: OG_E_INTERNAL (the check's
+ * details go to og_last_cuda_error), OG_E_TIMEOUT, OG_E_ARENA, OG_E_OVERFLOW, OG_OK. */
+int og_launch_status(uint32_t err, uint32_t bad_code, uint32_t bad_val, uint32_t bad_aux,
+                     uint32_t arena_out);
+/* Memory round-trip probe (a measurement aid; the paper has no counterpart): ctas x
+ * threads threads each follow a chain of hops dependent accesses through a fresh
+ * device array of bytes bytes (a power of two, 4 KiB .. 16 GiB; every hop lands far
+ * from the previous one), and *ns_per_hop receives the kernel time / hops, i.e. the
+ * round-trip time of one access with that many chains in flight.  mode 0: relaxed loads
+ * served by L2; 1: atomicMin whose result is used (the array is left unchanged); 2:
+ * non-coherent loads through L1.  Allocates and frees its array; synchronises the
+ * device.  OG_E_INVALID for bad sizes (threads a multiple of 32, at most 1024). */
+int og_probe_chain(uint32_t mode, uint64_t bytes, uint32_t ctas, uint32_t threads,
+                   uint32_t hops, double* ns_per_hop);
 const char* og_strerror(int code);
 const char* og_last_cuda_error(void);
 int og_version(void);

@@ -110,6 +110,8 @@ def lib():
             "og_last_cuda_error": (ctypes.c_char_p, []),
             "og_version": (i32, []),
             "og_sssp_delta_noalloc": (i32, [vp, vp, u32, u64, u32, u32, vp, vp]),
+            "og_launch_status": (i32, [u32, u32, u32, u32, u32]),
+            "og_probe_chain": (i32, [u32, u64, u32, u32, u32, P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -413,6 +415,21 @@ def sssp_delta_noalloc(offsets, edges, n: int, m: int, src: int, delta: int, out
     _check(lib().og_sssp_delta_noalloc(_ptr(offsets), _ptr(edges), n, m, src, delta, _ptr(out),
                                        _stream(stream)), "og_sssp_delta_noalloc")
     return out
+
+
+def launch_status(err: int, bad_code: int = 0, bad_val: int = 0, bad_aux: int = 0,
+                  arena_out: bool = False) -> int:
+    """Status the round-engine entry points derive from a launch's error word (no GPU
+    needed): OG_E_INTERNAL > OG_E_TIMEOUT > OG_E_ARENA > OG_E_OVERFLOW > OG_OK."""
+    return int(lib().og_launch_status(err, bad_code, bad_val, bad_aux, 1 if arena_out else 0))
+
+
+def probe_chain(mode: int, nbytes: int, ctas: int, threads: int, hops: int) -> float:
+    """ns per dependent access: mode 0 L2 loads, 1 atomicMin round trips, 2 L1 loads."""
+    v = ctypes.c_double(0.0)
+    _check(lib().og_probe_chain(mode, nbytes, ctas, threads, hops, ctypes.byref(v)),
+           "og_probe_chain")
+    return float(v.value)
 
 
 def version() -> int:

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -31,6 +32,8 @@ cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots,
                         cudaStream_t st);
 cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj, size_t m,
                               uint32_t n, uint32_t* flags, int sms, cudaStream_t st);
+cudaError_t launch_check_csr(const uint32_t* off, const uint2* adj, uint32_t n, uint32_t m,
+                             uint32_t* flags, int sms, cudaStream_t st);
 cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t st);
 cudaError_t async_occupancy(int* blocks_per_sm, size_t smem, bool ell);
 cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,
@@ -66,6 +69,27 @@ int cuda_fail(cudaError_t e, const char* what) {
     int _r = (x);                 \
     if (_r != OG_OK) return _r;   \
   } while (0)
+
+// Status of a finished persistent launch from the error word it left in Sync: a failed
+// internal bounds check first (its code, value and context go to the message), then a
+// bounded wait that gave up, then a query that ran out of bucket space where the arena
+// cannot grow (arena_out), then a saturated distance.  Every entry point that runs the
+// round engine maps its launches through this one function.
+int launch_status(uint32_t err, uint32_t bad_code, uint32_t bad_val, uint32_t bad_aux,
+                  bool arena_out) {
+  if (err & kErrBounds) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
+             bad_code, bad_val, bad_aux);
+    return OG_E_INTERNAL;
+  }
+  if (err & kErrTimeout) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "grid barrier wait gave up");
+    return OG_E_TIMEOUT;
+  }
+  if (arena_out) return OG_E_ARENA;
+  if (err & kErrSat) return OG_E_OVERFLOW;
+  return OG_OK;
+}
 
 struct DBuf {
   void* p = nullptr;
@@ -321,8 +345,9 @@ struct RunOut {
 // + i*n).
 int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
               uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)kBinCap * (sizeof(uint2) + sizeof(uint16_t));
-  const bool ell = c.layout == OG_LAYOUT_ELL && g->ell;
+  const size_t smem = delta_smem_bytes(kBinCap);
+  // The lazy bucket update marks vertices instead of inserting them: CSR kernel only.
+  const bool ell = c.layout == OG_LAYOUT_ELL && g->ell && c.bucket_update != OG_UPDATE_LAZY;
   TRY(occupancy(g, smem, ell));
   uint32_t min_delta = 0xFFFFFFFFu;
   bool astar = false;
@@ -439,15 +464,9 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     const Sync* hy = ws.h_sync.as<Sync>();
     const QState* hq = ws.h_qs.as<QState>();
     ro->err |= hy->err & ~(uint32_t)kErrArena;
-    if (hy->err & kErrBounds) {
-      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
-               hy->bad_code, hy->bad_val, hy->bad_aux);
-      return OG_E_INTERNAL;
-    }
-    if (hy->err & kErrTimeout) {
-      snprintf(g_cuda_msg, sizeof(g_cuda_msg), "grid barrier wait gave up");
-      return OG_E_TIMEOUT;
-    }
+    // Fatal errors end the call here; saturation is reported once every chunk has run,
+    // and an exhausted arena is regrown below.
+    TRY(launch_status(hy->err & kErrFatal, hy->bad_code, hy->bad_val, hy->bad_aux, false));
     pending.clear();
     for (uint32_t i = 0; i < nq; ++i)
       if (hq[i].aborted) pending.push_back(i);
@@ -737,8 +756,7 @@ int run_queries(og_graph* g, const og_query* qv, uint32_t nq, const og_config* u
     }
   }
   export_stats(acc, ro.restarts, stats);
-  if (ro.err & kErrSat) return OG_E_OVERFLOW;
-  return OG_OK;
+  return launch_status(ro.err & kErrSat, 0, 0, 0, false);
 }
 
 }  // namespace
@@ -1588,3 +1606,196 @@ int og_autotune_batch(og_graph* g, const og_query* queries, uint32_t nq, uint32_
 }
 
 }  // extern "C"
+
+// ---- allocation-free entry point ----------------------------------------------------------
+// og_sssp_delta_noalloc runs the same round-synchronous kernel as og_sssp_delta, but its
+// scratch (query cursor, barrier words, counters, bucket ring and overflow pile) lives in
+// the fixed device array below instead of memory the library allocates.  It serves
+// callers that cannot call cudaMalloc: code inside a host application whose allocator has
+// already claimed the device memory, code on a path where cudaMalloc's implicit device
+// synchronisation is not acceptable, and code that must not meet an out-of-memory error
+// after start-up.  The array is reserved on every GPU that loads the library, for the
+// life of the process.
+namespace og {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;           // scratch array size (64 MiB)
+constexpr uint32_t kNoAllocMaxN = 1u << 20;             // largest graph accepted
+constexpr int kNoAllocMaxDevices = 64;
+constexpr uint32_t kNoAllocRing = kMaxRing;             // materialised buckets
+// Header of the array (byte offsets), then the bucket arena from kNoAllocHeader on.
+constexpr size_t kNaSync = 0, kNaStats = 256, kNaQDesc = 512, kNaQState = 768;
+constexpr size_t kNaPref = 1024, kNaCheck = 1536, kNaCounts = 2048, kNaHeader = 4096;
+static_assert(sizeof(Sync) <= kNaStats - kNaSync, "Sync overlaps Stats in the header");
+static_assert(sizeof(Stats) <= kNaQDesc - kNaStats, "Stats overlaps the query descriptor");
+static_assert(sizeof(QDesc) <= kNaQState - kNaQDesc, "QDesc overlaps the query state");
+static_assert(sizeof(QState) <= kNaPref - kNaQState, "QState overlaps the frontier prefix");
+static_assert(2 * sizeof(uint32_t) <= kNaCheck - kNaPref, "prefix (nq + 1 words) overflows");
+static_assert(sizeof(uint32_t) <= kNaCounts - kNaCheck, "check word overlaps the counters");
+static_assert(kNoAllocRing * sizeof(uint32_t) <= kNaHeader - kNaCounts,
+              "ring counters overflow the header");
+static_assert(kNaHeader % 256 == 0 && kNoAllocBytes > kNaHeader, "arena alignment");
+
+static __device__ __align__(256) unsigned char og_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+struct NoAllocDev {
+  unsigned long long ctx_id = 0;  // context the address below belongs to (0 = none yet)
+  void* ptr = nullptr;
+  int occ = 0, sms = 0;
+};
+NoAllocDev g_noalloc[kNoAllocMaxDevices];
+
+// Identifier of the calling thread's current CUDA context (unique for the life of the
+// process), through the driver entry points the runtime exposes: a context re-created
+// after cudaDeviceReset loads the module again, possibly at another address, and gets
+// a new identifier.  0 when it cannot be read.
+unsigned long long current_ctx_id() {
+  using GetCur = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<GetCur>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  if (!get_cur || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+}  // namespace
+
+}  // namespace og
+
+extern "C" int og_launch_status(uint32_t err, uint32_t bad_code, uint32_t bad_val,
+                                uint32_t bad_aux, uint32_t arena_out) {
+  return launch_status(err, bad_code, bad_val, bad_aux, arena_out != 0);
+}
+
+extern "C" int og_sssp_delta_noalloc(const uint32_t* offsets, const uint32_t* edges, uint32_t n,
+                                     uint64_t m, uint32_t src, uint32_t delta,
+                                     uint32_t* dist_out, void* stream) {
+  using namespace og;
+  if (!offsets || !dist_out || (m && !edges) || n == 0 || src >= n || delta == 0)
+    return OG_E_INVALID;
+  if (n > kNoAllocMaxN || m >= 0xFFFFFFFFull) return OG_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return OG_E_INVALID;
+  const size_t smem = delta_smem_bytes(kBinCap);
+  void* base = nullptr;
+  int occ = 0, sms = 0;
+  {
+    // Set-up, once per device (and again if the device's context was re-created), with
+    // that device current: the device address of the array -- in host code the array's
+    // name is only a host-side stand-in -- and the launch shape.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDev& d = g_noalloc[dev];
+    const unsigned long long ctx = current_ctx_id();
+    if (!d.ptr || ctx == 0 || ctx != d.ctx_id) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, og_noalloc_scratch));
+      if (!p) return OG_E_CUDA;
+      if (!d.occ) {
+        CK(delta_occupancy(&d.occ, smem, false));
+        CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        if (d.occ < 1) {
+          snprintf(g_cuda_msg, sizeof(g_cuda_msg), "persistent kernel does not fit on an SM");
+          return OG_E_CUDA;
+        }
+      }
+      d.ptr = p;
+      d.ctx_id = ctx;
+    }
+    base = d.ptr;
+    occ = d.occ;
+    sms = d.sms;
+  }
+  unsigned char* b = static_cast<unsigned char*>(base);
+  Sync* sync = reinterpret_cast<Sync*>(b + kNaSync);
+  Stats* stats = reinterpret_cast<Stats*>(b + kNaStats);
+  QDesc* qd = reinterpret_cast<QDesc*>(b + kNaQDesc);
+  QState* qs = reinterpret_cast<QState*>(b + kNaQState);
+  uint32_t* pref = reinterpret_cast<uint32_t*>(b + kNaPref);
+  uint32_t* check = reinterpret_cast<uint32_t*>(b + kNaCheck);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(b + kNaCounts);
+  // The weights are not scanned, so the widest ring is used (a relaxation may jump up
+  // to kNoAllocRing - 1 buckets before it spills to the overflow pile).
+  const uint32_t B = kNoAllocRing;
+  const uint64_t arena = (kNoAllocBytes - kNaHeader) / sizeof(uint2);
+  const uint32_t cap = (uint32_t)(arena / 2 / B);
+  const uint32_t ocap = (uint32_t)(arena / 4);
+  uint2* ring = reinterpret_cast<uint2*>(b + kNaHeader);
+  uint2* ovf = ring + (size_t)B * cap;
+  const uint2* adj = reinterpret_cast<const uint2*>(edges);
+
+  // Calls share the array: its state words start from zero on every call (two calls
+  // that overlap on the GPU would race on them).  The caller's graph is checked first
+  // and the search only runs on a well-formed one.
+  uint32_t hcheck = 0;
+  CK(cudaMemsetAsync(b, 0, kNaHeader, st));
+  CK(launch_check_csr(offsets, adj, n, (uint32_t)m, check, sms, st));
+  CK(cudaMemcpyAsync(&hcheck, check, sizeof(hcheck), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hcheck) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "graph rejected:%s%s",
+             (hcheck & 1u) ? " offsets not 0 .. m and non-decreasing" : "",
+             (hcheck & 2u) ? " a neighbor id >= n" : "");
+    return OG_E_INVALID;
+  }
+
+  QDesc hq;
+  memset(&hq, 0, sizeof(hq));
+  hq.src = src;
+  hq.dst = kNone;
+  hq.delta = delta;
+  hq.kind = kSSSP;
+  Params P{};
+  P.off = offsets;
+  P.adj = adj;
+  P.xy = nullptr;
+  P.n = n;
+  P.dist = dist_out;
+  P.qd = qd;
+  P.qs = qs;
+  P.ring = ring;
+  P.counts = counts;
+  P.ovf = ovf;
+  P.fr_pref = pref;
+  P.sync = sync;
+  P.stats = stats;
+  P.hub_min = 0xFFFFFFFFu;  // no hub list (it would need more scratch)
+  P.nq = 1;
+  P.B = B;
+  P.Bmask = B - 1;
+  P.cap = cap;
+  P.ocap = ocap;
+  P.T = kDefaultFusion;
+  P.tile = 128;
+  P.bin_cap = kBinCap;
+  P.max_rounds = 0xFFFFFFFFu;
+  P.has_astar = 0;
+  P.spin_ns = kDefaultSpinNs;
+  CK(cudaMemcpyAsync(qd, &hq, sizeof(hq), cudaMemcpyHostToDevice, st));
+  CK(launch_fill(dist_out, n, nullptr, 1, sms, st));
+  CK(launch_init(P, nullptr, 1, st));
+  CK(launch_delta(P, sms * occ, smem, st));
+  Sync hs;
+  QState hqs;
+  CK(cudaMemcpyAsync(&hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hqs, qs, sizeof(hqs), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return launch_status(hs.err, hs.bad_code, hs.bad_val, hs.bad_aux, hqs.aborted != 0);
+}

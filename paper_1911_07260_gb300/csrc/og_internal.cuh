@@ -23,6 +23,17 @@ constexpr int kBlock = 256;              // threads per persistent CTA
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxQ = 512;               // queries per launch
 constexpr int kMaxRing = 256;            // materialised buckets per query
+constexpr uint32_t kOutbox = 512;        // staged entries of later buckets per CTA
+
+// Dynamic shared memory of the round engine's persistent kernel: two CTA-local bins of
+// bin_cap entries ({vertex, distance} + 16-bit query), then the outbox of kOutbox
+// {vertex, distance, query, bucket} entries (16-byte aligned).
+__host__ __device__ constexpr size_t bins_smem_bytes(uint32_t bin_cap) {
+  return ((size_t)2 * bin_cap * (sizeof(uint2) + sizeof(uint16_t)) + 15) & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t delta_smem_bytes(uint32_t bin_cap) {
+  return bins_smem_bytes(bin_cap) + (size_t)kOutbox * sizeof(uint4);
+}
 
 // kBF: unordered Bellman-Ford; its QDesc.delta is 0 and every insert goes to bucket
 // cur + 1, so a bucket is one round's frontier.

@@ -31,12 +31,15 @@ struct Smem {
   uint32_t delta[kMaxQ];
   uint32_t head[kMaxQ];    // frontier start in the current ring slot
   uint32_t pref[kMaxQ + 1];// frontier prefix sums (scratch in the decider)
-  uint32_t binN[2];        // CTA-local bin fill counts
+  uint32_t binN[3];        // CTA-local bin fill counts (a level reads one, fills the
+                           // next and clears the third)
+  uint32_t obN;            // entries staged in the outbox this round
   uint32_t grab;
   uint32_t last;
   uint32_t phase;
   uint32_t err;
   uint32_t f_active, f_redist;
+  uint32_t d_err, d_big, d_lz;  // decider: control words read once by thread 0
   uint32_t wtmp[kWarps + 1];
   uint32_t lb_pos[kBlock + 1];  // CTA-wide expansion: edge prefix sums of the entries
   uint32_t lb_beg[kBlock], lb_g[kBlock], lb_q[kBlock];
@@ -46,6 +49,14 @@ struct Smem {
 struct Bins {
   uint2* e[2];
   uint16_t* q[2];
+  uint4* ob;     // outbox: {vertex, distance, query, bucket} of later buckets, this round
+};
+
+// The CTA-local bin a level fills: its entries, their queries and its fill count.
+struct BinOut {
+  uint2* e;
+  uint16_t* q;
+  uint32_t* n;
 };
 
 struct Cnt {
@@ -56,7 +67,7 @@ struct Cnt {
 // bin when the bucket is the query's current one and fusion is on, else the ring slot of
 // the bucket (warp-aggregated: lanes with the same (query, slot) share one atomicAdd),
 // else the overflow pile.  Must be called by all 32 lanes.
-__device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins& B, int out,
+__device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const BinOut& O,
                                             bool ins, bool allow_local, uint32_t v,
                                             uint32_t nd, uint32_t key, uint32_t q, Cnt& C) {
   const uint32_t lane = threadIdx.x & 31;
@@ -74,13 +85,13 @@ __device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const Bins
   if (lm) {
     const int leader = __ffs(lm) - 1;
     uint32_t base = 0;
-    if ((int)lane == leader) base = atomicAdd(&S.binN[out], (uint32_t)__popc(lm));
+    if ((int)lane == leader) base = atomicAdd(O.n, (uint32_t)__popc(lm));
     base = __shfl_sync(FULL, base, leader);
     if (dest == 1) {
       const uint32_t pos = base + __popc(lm & lanemask_lt());
       if (pos < P.bin_cap) {
-        B.e[out][pos] = make_uint2(v, nd);
-        B.q[out][pos] = (uint16_t)q;
+        O.e[pos] = make_uint2(v, nd);
+        O.q[pos] = (uint16_t)q;
         C.local++;
       } else {
         dest = 2;  // bin full: the entry goes to the global current bucket
@@ -142,7 +153,7 @@ __device__ __forceinline__ void mark_warp(const Params& P, bool first, uint32_t 
 // atomics are issued before any insert, so a lane keeps K independent memory operations
 // in flight instead of paying one round trip per edge.
 template <int K>
-__device__ __forceinline__ void relax_edges(const Params& P, Smem& S, const Bins& B, int out,
+__device__ __forceinline__ void relax_edges(const Params& P, Smem& S, const BinOut& O,
                                             bool allow_local, const bool (&ok)[K],
                                             const uint2 (&ew)[K], const uint32_t (&g)[K],
                                             const uint32_t (&q)[K], Cnt& C) {
@@ -201,20 +212,20 @@ __device__ __forceinline__ void relax_edges(const Params& P, Smem& S, const Bins
     // Delta 0 marks a Bellman-Ford query: the next round's bucket, whatever the distance.
     const uint32_t dq = S.delta[q[k]];
     const uint32_t key = ins ? (dq ? bucket_of(nd[k], h[k], dq) : S.cur[q[k]] + 1u) : 0u;
-    insert_warp(P, S, B, out, ins, allow_local, ew[k].x, nd[k], key, q[k], C);
+    insert_warp(P, S, O, ins, allow_local, ew[k].x, nd[k], key, q[k], C);
   }
 }
 
 // CSR edges: the K neighbor loads are issued together, then relax_edges.
 template <int K>
-__device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const Bins& B, int out,
+__device__ __forceinline__ void relax_batch(const Params& P, Smem& S, const BinOut& O,
                                             bool allow_local, const bool (&ok)[K],
                                             const uint32_t (&e)[K], const uint32_t (&g)[K],
                                             const uint32_t (&q)[K], Cnt& C) {
   uint2 ew[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) ew[k] = ok[k] ? __ldg(P.adj + e[k]) : make_uint2(0u, 0u);
-  relax_edges<K>(P, S, B, out, allow_local, ok, ew, g, q, C);
+  relax_edges<K>(P, S, O, allow_local, ok, ew, g, q, C);
 }
 
 constexpr int kLightBatch = 4;  // light-edge groups of 32 relaxed per batch
@@ -251,40 +262,10 @@ __device__ __noinline__ bool push_hub(const Params& P, uint32_t u, uint32_t g, u
 // Vertices with >= 32 edges are expanded by the whole warp one at a time; the others are
 // flattened into one edge list that the 32 lanes walk together, so consecutive lanes
 // read consecutive edges of a vertex.  Must be called by all 32 lanes.
-template <bool ELL>
-__device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins& B, int out,
+__device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const BinOut& O,
                                             bool allow_local, bool has, uint32_t u,
                                             uint32_t g, uint32_t q, Cnt& C) {
   const uint32_t lane = threadIdx.x & 31;
-  if (ELL) {
-    // ELL rows: each lane reads its vertex's whole row (64 bytes, no offsets lookup) in
-    // parallel with the stale check and relaxes its up to 8 edges together.
-    uint2 ew[kEllWidth];
-    bool live = has;
-    uint32_t d = 0;
-    if (has) {
-      C.items++;
-      d = __ldcg(P.dist + (size_t)q * P.n + u);
-      load_row(P.ell, u, ew);
-    } else {
-#pragma unroll
-      for (int k = 0; k < kEllWidth; ++k) ew[k] = make_uint2(kNone, 0u);
-    }
-    if (has && d != g) {
-      live = false;
-      C.stale++;
-    }
-    bool ok[kEllWidth];
-    uint32_t gg[kEllWidth], qq[kEllWidth];
-#pragma unroll
-    for (int k = 0; k < kEllWidth; ++k) {
-      ok[k] = live && ew[k].x != kNone;
-      gg[k] = g;
-      qq[k] = q;
-    }
-    relax_edges<kEllWidth>(P, S, B, out, allow_local, ok, ew, gg, qq, C);
-    return;
-  }
   uint32_t beg = 0, end = 0;
   if (has) {
     C.items++;
@@ -315,7 +296,7 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
         gg[k] = hg;
         qq[k] = hq;
       }
-      relax_batch<kHeavyBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
+      relax_batch<kHeavyBatch>(P, S, O, allow_local, ok, ee, gg, qq, C);
     }
   }
   const uint32_t ld = heavy ? 0u : end - beg;
@@ -345,8 +326,184 @@ __device__ __forceinline__ void expand_warp(const Params& P, Smem& S, const Bins
       ok[k] = idx < total;
       ee[k] = ob + (idx - oe);
     }
-    relax_batch<kLightBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
+    relax_batch<kLightBatch>(P, S, O, allow_local, ok, ee, gg, qq, C);
   }
+}
+
+// Stages entries of later buckets (lanes with bits in gm; their vertex, distance and
+// bucket in ew / nd / key) in the CTA's outbox, which reaches the global buckets once at
+// the end of the round (flush_outbox), so the level that produced them does not wait for
+// a global atomic.  Entries that do not fit go to their buckets directly.  All 32 lanes.
+template <bool ASTAR>
+__device__ __forceinline__ void stage_later(const Params& P, Smem& S, const Bins& B,
+                                            const BinOut& O, unsigned gm,
+                                            const uint2 (&ew)[kEllWidth],
+                                            const uint32_t (&nd)[kEllWidth], uint32_t q,
+                                            bool astar, Cnt& C) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t cq = S.cur[q], dl = S.delta[q];
+  uint32_t key[kEllWidth];  // the bucket of each staged entry, as expand_rows chose it
+#pragma unroll
+  for (int k = 0; k < kEllWidth; ++k) {
+    const uint32_t h = (ASTAR && astar && ((gm >> k) & 1u))
+                           ? heuristic(P.xy, P.xy_integral, ew[k].x, __ldg(&P.qd[q].tx),
+                                       __ldg(&P.qd[q].ty))
+                           : 0u;
+    const uint32_t kk = dl ? bucket_of(nd[k], h, dl) : cq + 1u;
+    key[k] = kk < cq ? cq : kk;
+  }
+  const uint32_t ng = __popc(gm);
+  uint32_t incl = ng;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, incl, o);
+    if ((int)lane >= o) incl += t;
+  }
+  uint32_t base = 0;
+  if (lane == 31) base = atomicAdd(&S.obN, incl);
+  base = __shfl_sync(FULL, base, 31);
+  uint32_t pos = base + incl - ng;
+  unsigned dm = 0;  // entries the outbox could not take
+#pragma unroll
+  for (int k = 0; k < kEllWidth; ++k) {
+    if ((gm >> k) & 1u) {
+      if (pos < kOutbox) B.ob[pos] = make_uint4(ew[k].x, nd[k], q, key[k]);
+      else dm |= 1u << k;
+      ++pos;
+    }
+  }
+  // One entry per lane per pass (selected by index, so insert_warp is expanded once).
+  while (__any_sync(FULL, dm != 0u)) {
+    const bool has = dm != 0u;
+    uint32_t v = 0, dv = 0, kv = 0;
+    if (has) {
+      const int j = __ffs(dm) - 1;
+      dm &= dm - 1u;
+#pragma unroll
+      for (int k = 0; k < kEllWidth; ++k) {
+        if (k == j) {
+          v = ew[k].x;
+          dv = nd[k];
+          kv = key[k];
+        }
+      }
+    }
+    insert_warp(P, S, O, has, false, v, dv, kv, q, C);
+  }
+}
+
+// Moves the outbox into the global buckets (ring slot or overflow pile, warp-aggregated).
+// Called by every thread of the CTA; leaves the outbox empty.
+__device__ void flush_outbox(const Params& P, Smem& S, const Bins& B, const BinOut& O, Cnt& C) {
+  __syncthreads();
+  const uint32_t n = min(S.obN, kOutbox);
+  const uint32_t lim = (n + 31u) & ~31u;
+  for (uint32_t k = threadIdx.x; k < lim; k += kBlock) {
+    const bool has = k < n;
+    uint4 en = make_uint4(0, 0, 0, 0);
+    if (has) en = B.ob[k];
+    insert_warp(P, S, O, has, false, en.x, en.y, en.w, en.z, C);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S.obN = 0;
+}
+
+// Expands the bucket entries held by a warp (one per lane with has) on the ELL layout:
+// the lane reads its vertex's whole row (up to 8 {neighbor, weight} pairs, 64 bytes)
+// together with the stale check, then issues the row's atomicMins, so a level costs
+// two dependent memory round trips.  Improved vertices of the current bucket go to the
+// CTA's bin with one warp-wide scan and one shared-memory atomic; those of later
+// buckets are staged in the outbox.  All 32 lanes.
+template <bool ASTAR>
+__device__ __forceinline__ void expand_rows(const Params& P, Smem& S, const Bins& B,
+                                            const BinOut& O, bool allow_local, bool has,
+                                            uint32_t u, uint32_t g, uint32_t q, Cnt& C) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint2 ew[kEllWidth];
+  uint32_t d = 0;
+  if (has) {
+    C.items++;
+    d = __ldcg(P.dist + (size_t)q * P.n + u);
+    load_row(P.ell, u, ew);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k) ew[k] = make_uint2(kNone, 0u);
+  }
+  const bool live = has && d == g;
+  if (has && !live) C.stale++;
+  uint32_t* dq = P.dist + (size_t)q * P.n;
+  unsigned okm = 0;
+  uint32_t nd[kEllWidth];
+#pragma unroll
+  for (int k = 0; k < kEllWidth; ++k) {
+    const bool ok = live && ew[k].x != kNone;
+    okm |= (ok ? 1u : 0u) << k;
+    const unsigned long long sum = (unsigned long long)g + ew[k].y;
+    nd[k] = sum >= kSat ? kSat : (uint32_t)sum;
+    if (ok && sum >= kSat) atomicOr(&P.sync->err, kErrSat);
+  }
+  if (P.precheck) {
+    uint32_t seen[kEllWidth];
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k) seen[k] = ((okm >> k) & 1u) ? ld_cached(dq + ew[k].x) : 0u;
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k)
+      if (nd[k] >= seen[k]) okm &= ~(1u << k);
+  }
+  uint32_t old[kEllWidth];
+#pragma unroll
+  for (int k = 0; k < kEllWidth; ++k)
+    old[k] = ((okm >> k) & 1u) ? atomicMin(dq + ew[k].x, nd[k]) : 0u;
+  const uint32_t cq = S.cur[q], dl = S.delta[q];
+  // A* (priority g + h): the heuristic is needed only for the improved edges' buckets.
+  const bool astar = ASTAR && P.has_astar && live && __ldg(&P.qd[q].kind) == kASTAR;
+  unsigned lm = 0, gm = 0;
+#pragma unroll
+  for (int k = 0; k < kEllWidth; ++k) {
+    const bool ins = ((okm >> k) & 1u) && nd[k] < old[k];
+    const uint32_t h = (astar && ins) ? heuristic(P.xy, P.xy_integral, ew[k].x,
+                                                  __ldg(&P.qd[q].tx), __ldg(&P.qd[q].ty))
+                                      : 0u;
+    // Delta 0 marks a Bellman-Ford query: the next round's bucket, whatever the distance.
+    uint32_t kk = dl ? bucket_of(nd[k], h, dl) : cq + 1u;
+    if (ins && kk < cq) {  // only with an inconsistent A* heuristic: clamp, no early exit
+      kk = cq;
+      P.qs[q].no_exit = 1u;
+    }
+    const bool loc = ins && allow_local && kk == cq;
+    lm |= (loc ? 1u : 0u) << k;
+    gm |= ((ins && !loc) ? 1u : 0u) << k;
+    if (ins && P.prefetch) prefetch_row(P.ell, P.off, ew[k].x);
+  }
+  C.relax += __popc(okm);
+  C.improved += __popc(lm | gm);
+  if (__any_sync(FULL, lm != 0u)) {
+    const uint32_t nl = __popc(lm);
+    uint32_t incl = nl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, incl, o);
+      if ((int)lane >= o) incl += t;
+    }
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(O.n, incl);
+    base = __shfl_sync(FULL, base, 31);
+    uint32_t pos = base + incl - nl;
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k) {
+      if ((lm >> k) & 1u) {
+        if (pos < P.bin_cap) {
+          O.e[pos] = make_uint2(ew[k].x, nd[k]);
+          O.q[pos] = (uint16_t)q;
+          C.local++;
+        } else {
+          gm |= 1u << k;  // bin full: the entry goes to the global current bucket
+        }
+        ++pos;
+      }
+    }
+  }
+  if (__any_sync(FULL, gm != 0u)) stage_later<ASTAR>(P, S, B, O, gm, ew, nd, q, astar, C);
 }
 
 // Block-wide exclusive scan of a[0..n) in place (each thread scans a run of
@@ -394,7 +551,7 @@ __device__ void block_exscan(uint32_t* a, uint32_t n, uint32_t* wtmp) {
 // shared memory).  Thread t of a batch takes edge e0 + t, so a warp reads 32 consecutive
 // edges and one high-degree entry no longer holds up a single warp.  Hubs are listed for
 // the BIG phase instead.  Must be called by all threads of the CTA (CSR layout only).
-__device__ __forceinline__ void expand_cta(const Params& P, Smem& S, const Bins& B, int out,
+__device__ __forceinline__ void expand_cta(const Params& P, Smem& S, const BinOut& O,
                                            bool allow_local, bool has, uint32_t u,
                                            uint32_t g, uint32_t q, Cnt& C) {
   const uint32_t tid = threadIdx.x;
@@ -435,19 +592,31 @@ __device__ __forceinline__ void expand_cta(const Params& P, Smem& S, const Bins&
       gg[k] = S.lb_g[j];
       qq[k] = S.lb_q[j];
     }
-    relax_batch<kLightBatch>(P, S, B, out, allow_local, ok, ee, gg, qq, C);
+    relax_batch<kLightBatch>(P, S, O, allow_local, ok, ee, gg, qq, C);
   }
   __syncthreads();  // the lb arrays are refilled by the next call
 }
 
 // Run by the CTA that arrives last at a grid barrier, before it releases the others:
 // advances every query's bucket cursor and publishes the next phase and frontier.
+// Every value a decision depends on is read once -- the control words by thread 0 into
+// shared memory, each query's words by lane 0 of its warp and shuffled to the others --
+// so a word that changes while the decider runs (the error word, when a waiting CTA
+// times out) can never send the lanes of a warp down different paths.
 __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Sync* sy = P.sync;
-  const uint32_t err = ld_relaxed(&sy->err);
+  if (tid == 0) {
+    S.d_err = ld_relaxed(&sy->err);
+    S.d_big = (uint32_t)(ld_relaxed64(&sy->big_word) >> 32);
+    S.d_lz = ld_relaxed(&sy->lz_n);
+    S.f_active = 0;
+    S.f_redist = 0;
+  }
+  __syncthreads();
+  const uint32_t err = S.d_err;
   const bool fatal = (err & kErrFatal) != 0;
-  if (done_phase == kPhRelax && !fatal && (__ldcg(&sy->big_word) >> 32) > 0u) {
+  if (done_phase == kPhRelax && !fatal && S.d_big > 0u) {
     // Listed hubs first: the same round continues with the BIG phase.
     if (tid == 0) {
       sy->phase = kPhBig;
@@ -462,7 +631,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
     }
     done_phase = kPhRelax;
   }
-  if (done_phase == kPhRelax && !fatal && P.lazy && __ldcg(&sy->lz_n) > 0u) {
+  if (done_phase == kPhRelax && !fatal && P.lazy && S.d_lz > 0u) {
     // Lazy bucket update: the marked vertices make their insertions before the round ends.
     if (tid == 0) {
       sy->phase = kPhApply;
@@ -474,17 +643,12 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
     if (tid == 0) sy->lz_n = 0u;
     done_phase = kPhRelax;
   }
-  if (tid == 0) {
-    S.f_active = 0;
-    S.f_redist = 0;
-  }
-  __syncthreads();
   for (uint32_t q = warp; q < P.nq; q += kWarps) {
     QState* qs = P.qs + q;
     uint32_t* cnts = P.counts + (size_t)q * P.B;
-    uint32_t active = __ldcg(&qs->active);
+    uint32_t active = warp_ld(&qs->active);
     uint32_t size = 0;
-    if (active && __ldcg(&qs->aborted)) {
+    if (active && warp_ld(&qs->aborted)) {
       active = 0;
       if (lane == 0) {
         qs->active = 0;
@@ -493,11 +657,11 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
       }
     }
     if (active && !fatal) {
-      uint32_t cur = __ldcg(&qs->cur), head = __ldcg(&qs->head), tail = __ldcg(&qs->tail);
-      uint32_t redist = __ldcg(&qs->redist);
+      uint32_t cur = warp_ld(&qs->cur), head = warp_ld(&qs->head), tail = warp_ld(&qs->tail);
+      uint32_t redist = warp_ld(&qs->redist);
       if (done_phase == kPhRelax) {
         const uint32_t c = cur & P.Bmask;
-        const uint32_t cnt = min(__ldcg(cnts + c), P.cap);
+        const uint32_t cnt = min(warp_ld(cnts + c), P.cap);
         if (cnt > tail) {  // the current bucket received entries: process it again
           head = tail;
           tail = cnt;
@@ -514,7 +678,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
           }
           __syncwarp();
           if (lane == 0) cnts[c] = 0u;
-          const uint32_t ovf_n = __ldcg(&qs->ovf_n), ovf_min = __ldcg(&qs->ovf_min);
+          const uint32_t ovf_n = warp_ld(&qs->ovf_n), ovf_min = warp_ld(&qs->ovf_min);
           if (ovf_n > 0 && ovf_min <= next) {
             redist = 1;
             if (lane == 0) {
@@ -527,11 +691,11 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
           } else {
             cur = next;
             head = 0;
-            tail = min(__ldcg(cnts + (next & P.Bmask)), P.cap);
+            tail = min(warp_ld(cnts + (next & P.Bmask)), P.cap);
           }
         }
       } else if (done_phase == kPhRedistMin && redist) {
-        const uint32_t nc = __ldcg(&qs->redist_min);
+        const uint32_t nc = warp_ld(&qs->redist_min);
         if (nc == kInf) {  // every pile entry was out of date and the ring is empty
           active = 0;
           redist = 0;
@@ -540,32 +704,34 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
           cur = nc;
         }
       } else if (done_phase == kPhRedistMove && redist) {
+        const uint32_t sel = warp_ld(&qs->ovf_sel), n2 = warp_ld(&qs->ovf_n2);
+        const uint32_t min2 = warp_ld(&qs->ovf_min2);
         if (lane == 0) {
-          qs->ovf_sel = __ldcg(&qs->ovf_sel) ^ 1u;
-          qs->ovf_n = __ldcg(&qs->ovf_n2);
-          qs->ovf_min = __ldcg(&qs->ovf_min2);
+          qs->ovf_sel = sel ^ 1u;
+          qs->ovf_n = n2;
+          qs->ovf_min = min2;
         }
         redist = 0;
         head = 0;
-        tail = min(__ldcg(cnts + (cur & P.Bmask)), P.cap);
+        tail = min(warp_ld(cnts + (cur & P.Bmask)), P.cap);
       }
       const QDesc* qd = P.qd + q;
       const uint32_t kind = __ldg(&qd->kind);
       const uint32_t dst = __ldg(&qd->dst);
-      if (active && !redist && (kind == kPPSP || kind == kASTAR) && !__ldcg(&qs->no_exit)) {
+      if (active && !redist && (kind == kPPSP || kind == kASTAR) && !warp_ld(&qs->no_exit)) {
         // Stop rule of Section 6.1 (PPSP): entering bucket i with i * Delta >= the best
         // distance to the target found so far.
-        const uint32_t dt = __ldcg(P.dist + (size_t)q * P.n + dst);
+        const uint32_t dt = warp_ld(P.dist + (size_t)q * P.n + dst);
         if (dt != kInf && (unsigned long long)cur * __ldg(&qd->delta) >= dt) active = 0;
       }
+      const uint32_t res = (!active && dst < P.n) ? warp_ld(P.dist + (size_t)q * P.n + dst) : 0u;
       if (lane == 0) {
         qs->cur = cur;
         qs->head = head;
         qs->tail = tail;
         qs->redist = redist;
         qs->active = active;
-        if (!active)
-          qs->result = dst < P.n ? __ldcg(P.dist + (size_t)q * P.n + dst) : 0u;
+        if (!active) qs->result = res;
         if (active) S.f_active = 1;
         if (redist) S.f_redist = 1;
       }
@@ -644,8 +810,12 @@ __device__ void grid_barrier(const Params& P, Smem& S, uint32_t& bar, uint32_t d
 
 // One round for all active queries: frontier pass over the global current buckets, then
 // the CTA-local fusion loop (Section 3.3): the CTA's warps drain its local bin together,
-// one level per iteration, with block-level synchronisation only.
-template <bool ELL>
+// one level per iteration, with block-level synchronisation only.  Entry buffers
+// alternate between two bins; their fill counts rotate over three words, so the count a
+// level fills was cleared during the level before and one barrier per level suffices.
+// On the ELL layout with fusion, entries of later buckets collect in the outbox and
+// reach the global buckets at the end of the round.
+template <bool ELL, bool ASTAR>
 __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uint32_t& fused) {
   const uint32_t tid = threadIdx.x;
   for (uint32_t q = tid; q < P.nq; q += kBlock) {
@@ -657,10 +827,13 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
     S.pref[P.nq] = __ldcg(P.fr_pref + P.nq);
     S.binN[0] = 0;
     S.binN[1] = 0;
+    S.binN[2] = 0;
+    S.obN = 0;
   }
   __syncthreads();
   const uint32_t total = S.pref[P.nq];
   const bool fuse = P.T != 0;
+  const BinOut first = {B.e[0], B.q[0], &S.binN[0]};
   const uint64_t t_start = tid == 0 ? gtimer() : 0ull;
   for (;;) {
     if (tid == 0) S.grab = atomicAdd(&P.sync->work, P.tile);
@@ -686,20 +859,29 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
         u = en.x;
         g = en.y;
       }
-      if constexpr (ELL) expand_warp<true>(P, S, B, 0, fuse, has, u, g, q, C);
-      else expand_cta(P, S, B, 0, fuse, has, u, g, q, C);
+      if constexpr (ELL) expand_rows<ASTAR>(P, S, B, first, fuse, has, u, g, q, C);
+      else expand_cta(P, S, first, fuse, has, u, g, q, C);
     }
   }
   const uint64_t t_mid = tid == 0 ? gtimer() : 0ull;
   if (tid == 0) S.t_front += t_mid - t_start;
-  if (!fuse) return;
-  int in = 0;
+  if (!fuse) {
+    if constexpr (ELL) flush_outbox(P, S, B, first, C);
+    return;
+  }
+  int in = 0;    // entry buffer the level reads
+  int cin = 0;   // count word of that buffer
   for (;;) {
     __syncthreads();
-    const uint32_t nin = S.binN[in];
+    const uint32_t nin = S.binN[cin];
     if (nin == 0) break;
+    const int cout = cin == 2 ? 0 : cin + 1;
+    // The third count word was read at the top of the previous level and is filled by
+    // the next one: clear it now.
+    if (tid == 0) S.binN[cout == 2 ? 0 : cout + 1] = 0;
     const uint32_t cnt = min(nin, P.bin_cap);
     const uint32_t lim = (cnt + 31u) & ~31u;
+    const BinOut O = {B.e[in ^ 1], B.q[in ^ 1], &S.binN[cout]};
     if (nin >= P.T) {
       // Large local bucket: hand it to the global bucket for the next round.
       for (uint32_t k = tid; k < lim; k += kBlock) {
@@ -710,10 +892,8 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
           en = B.e[in][k];
           q = B.q[in][k];
         }
-        insert_warp(P, S, B, in ^ 1, has, false, en.x, en.y, has ? S.cur[q] : 0u, q, C);
+        insert_warp(P, S, O, has, false, en.x, en.y, has ? S.cur[q] : 0u, q, C);
       }
-      __syncthreads();
-      if (tid == 0) S.binN[in] = 0;
       break;
     }
     for (uint32_t k = tid; k < lim; k += kBlock) {
@@ -724,13 +904,14 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
         en = B.e[in][k];
         q = B.q[in][k];
       }
-      expand_warp<ELL>(P, S, B, in ^ 1, true, has, en.x, en.y, q, C);
+      if constexpr (ELL) expand_rows<ASTAR>(P, S, B, O, true, has, en.x, en.y, q, C);
+      else expand_warp(P, S, O, true, has, en.x, en.y, q, C);
     }
-    __syncthreads();
-    if (tid == 0) S.binN[in] = 0;
     in ^= 1;
+    cin = cout;
     ++fused;
   }
+  if constexpr (ELL) flush_outbox(P, S, B, first, C);
   __syncthreads();
   if (tid == 0) S.t_fused += gtimer() - t_mid;
 }
@@ -740,9 +921,9 @@ __device__ void redist_min_phase(const Params& P) {
   const uint32_t gtid = blockIdx.x * kBlock + threadIdx.x, gstride = gridDim.x * kBlock;
   for (uint32_t q = 0; q < P.nq; ++q) {
     QState* qs = P.qs + q;
-    if (!__ldcg(&qs->redist)) continue;
-    const uint32_t sel = __ldcg(&qs->ovf_sel);
-    const uint32_t n = min(__ldcg(&qs->ovf_n), P.ocap);
+    if (!warp_ld(&qs->redist)) continue;
+    const uint32_t sel = warp_ld(&qs->ovf_sel);
+    const uint32_t n = min(warp_ld(&qs->ovf_n), P.ocap);
     const QDesc* qd = P.qd + q;
     const bool astar = __ldg(&qd->kind) == kASTAR;
     const uint32_t delta = __ldg(&qd->delta);
@@ -766,10 +947,10 @@ __device__ void redist_move_phase(const Params& P) {
   const uint32_t gtid = blockIdx.x * kBlock + threadIdx.x, gstride = gridDim.x * kBlock;
   for (uint32_t q = 0; q < P.nq; ++q) {
     QState* qs = P.qs + q;
-    if (!__ldcg(&qs->redist)) continue;
-    const uint32_t sel = __ldcg(&qs->ovf_sel);
-    const uint32_t n = min(__ldcg(&qs->ovf_n), P.ocap);
-    const uint32_t cur = __ldcg(&qs->cur);
+    if (!warp_ld(&qs->redist)) continue;
+    const uint32_t sel = warp_ld(&qs->ovf_sel);
+    const uint32_t n = min(warp_ld(&qs->ovf_n), P.ocap);
+    const uint32_t cur = warp_ld(&qs->cur);
     const QDesc* qd = P.qd + q;
     const bool astar = __ldg(&qd->kind) == kASTAR;
     const uint32_t delta = __ldg(&qd->delta);
@@ -809,20 +990,24 @@ __device__ void redist_move_phase(const Params& P) {
 // buckets.
 __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const BinOut O = {B.e[0], B.q[0], &S.binN[0]};  // never written: hub edges go global
   const uint64_t t_start = tid == 0 ? gtimer() : 0ull;
   for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
   __syncthreads();
-  const uint32_t nsub = min((uint32_t)__ldcg(&P.sync->big_word), P.map_cap) * kBigSubs;
+  const uint32_t nsub =
+      min(warp_ld(reinterpret_cast<const uint32_t*>(&P.sync->big_word)), P.map_cap) * kBigSubs;
   for (;;) {
     uint32_t c = 0;
     if (lane == 0) c = atomicAdd(&P.sync->big_claim, 1u);
     c = __shfl_sync(FULL, c, 0);
     if (c >= nsub) break;
-    const uint32_t slot = __ldcg(P.big_map + c / kBigSubs);
+    // Lane 0 reads the piece's hub and shuffles it: the loop bounds below enclose
+    // full-warp collectives, so every lane must see the same values.
+    const uint32_t slot = warp_ld(P.big_map + c / kBigSubs);
     if (slot >= P.big_cap) continue;  // chunk of a hub that did not fit (expanded in place)
     const BigItem* it = P.big + slot;
-    const uint32_t hb = __ldcg(&it->beg), he = __ldcg(&it->end);
-    const uint32_t hg = __ldcg(&it->g), hq = __ldcg(&it->q), cb = __ldcg(&it->cbase);
+    const uint32_t hb = warp_ld(&it->beg), he = warp_ld(&it->end);
+    const uint32_t hg = warp_ld(&it->g), hq = warp_ld(&it->q), cb = warp_ld(&it->cbase);
     const uint32_t e0 = hb + (c / kBigSubs - cb) * kBigChunk + (c % kBigSubs) * kBigSub;
     for (uint32_t s0 = e0; s0 < min(he, e0 + kBigSub); s0 += 32 * kHeavyBatch) {
       bool ok[kHeavyBatch];
@@ -834,7 +1019,7 @@ __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
         gg[k] = hg;
         qq[k] = hq;
       }
-      relax_batch<kHeavyBatch>(P, S, B, 0, false, ok, ee, gg, qq, C);
+      relax_batch<kHeavyBatch>(P, S, O, false, ok, ee, gg, qq, C);
     }
   }
   __syncthreads();
@@ -846,9 +1031,10 @@ __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
 // updates); its mark is cleared for the next round.
 __device__ void lazy_apply_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   const uint32_t tid = threadIdx.x;
+  const BinOut O = {B.e[0], B.q[0], &S.binN[0]};  // never written: inserts go global
   for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
   __syncthreads();
-  const uint32_t tn = min(__ldcg(&P.sync->lz_n), P.lz_cap);
+  const uint32_t tn = min(warp_ld(&P.sync->lz_n), P.lz_cap);
   for (uint32_t i0 = blockIdx.x * kBlock; i0 < tn; i0 += gridDim.x * kBlock) {
     const uint32_t i = i0 + tid;
     bool has = i < tn;
@@ -871,11 +1057,11 @@ __device__ void lazy_apply_phase(const Params& P, Smem& S, const Bins& B, Cnt& C
         has = false;
       }
     }
-    insert_warp(P, S, B, 0, has, false, v, d, key, q, C);
+    insert_warp(P, S, O, has, false, v, d, key, q, C);
   }
 }
 
-template <bool ELL>
+template <bool ELL, bool ASTAR>
 __device__ __forceinline__ void delta_body(const Params& P) {
   extern __shared__ __align__(16) unsigned char og_dyn_smem[];
   __shared__ Smem S;
@@ -884,6 +1070,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
   B.e[1] = B.e[0] + P.bin_cap;
   B.q[0] = reinterpret_cast<uint16_t*>(B.e[1] + P.bin_cap);
   B.q[1] = B.q[0] + P.bin_cap;
+  B.ob = reinterpret_cast<uint4*>(og_dyn_smem + bins_smem_bytes(P.bin_cap));
   for (uint32_t q = threadIdx.x; q < P.nq; q += kBlock) S.delta[q] = __ldg(&P.qd[q].delta);
   Cnt C = {0, 0, 0, 0, 0, 0, 0};
   uint32_t fused = 0;
@@ -893,7 +1080,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
   for (;;) {
     const uint32_t phase = S.phase;
     if (phase == kPhStop || (S.err & kErrFatal)) break;
-    if (phase == kPhRelax) relax_phase<ELL>(P, S, B, C, fused);
+    if (phase == kPhRelax) relax_phase<ELL, ASTAR>(P, S, B, C, fused);
     else if (phase == kPhRedistMin) redist_min_phase(P);
     else if (phase == kPhRedistMove) redist_move_phase(P);
     else if (phase == kPhApply) lazy_apply_phase(P, S, B, C);
@@ -920,12 +1107,17 @@ __device__ __forceinline__ void delta_body(const Params& P) {
 }
 
 // The persistent kernel, one instantiation per adjacency layout (CSR offsets + edge
-// array for any graph; ELL-8 rows for graphs of degree at most 8).
+// array for any graph; ELL-8 rows for graphs of degree at most 8).  On ELL rows, launches
+// with an A* query use their own instantiation, so the heuristic's registers do not
+// weigh on the others.
 extern "C" __global__ void __launch_bounds__(kBlock, 3) og_delta_kernel(Params P) {
-  delta_body<false>(P);
+  delta_body<false, true>(P);
 }
 extern "C" __global__ void __launch_bounds__(kBlock, 3) og_delta_ell_kernel(Params P) {
-  delta_body<true>(P);
+  delta_body<true, false>(P);
+}
+extern "C" __global__ void __launch_bounds__(kBlock, 3) og_delta_ell_astar_kernel(Params P) {
+  delta_body<true, true>(P);
 }
 
 // dist[slot][*] = unreachable for the listed slots (blockIdx.y indexes the slot list).
@@ -1033,17 +1225,33 @@ cudaError_t launch_ell(const uint32_t* off, const uint2* adj, uint4* ell, uint32
 }
 
 // Host-side launchers (the kernels above are only launched through these).
+static const void* delta_kernel_for(bool ell, bool astar) {
+  if (!ell) return (const void*)og_delta_kernel;
+  return astar ? (const void*)og_delta_ell_astar_kernel : (const void*)og_delta_ell_kernel;
+}
+
 cudaError_t launch_delta(const Params& P, int grid, size_t smem, cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P)};
-  const void* k = P.ell ? (const void*)og_delta_ell_kernel : (const void*)og_delta_kernel;
+  const void* k = delta_kernel_for(P.ell != nullptr, P.has_astar != 0);
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kBlock), args, smem, st);
 }
 
+// CTAs per SM of the persistent kernel for a layout (the smaller of the two ELL
+// instantiations, so one launch shape serves both); also sets its shared-memory limit.
 cudaError_t delta_occupancy(int* blocks_per_sm, size_t smem, bool ell) {
-  const void* k = ell ? (const void*)og_delta_ell_kernel : (const void*)og_delta_kernel;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
+  int best = 1 << 30;
+  for (int a = 0; a < (ell ? 2 : 1); ++a) {
+    const void* k = delta_kernel_for(ell, a == 1);
+    cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kBlock, smem);
+    if (e != cudaSuccess) return e;
+    best = b < best ? b : best;
+  }
+  *blocks_per_sm = best;
+  return cudaSuccess;
 }
 
 cudaError_t launch_fill(uint32_t* dist, uint32_t n, const uint32_t* slots, uint32_t nslots,
@@ -1069,144 +1277,31 @@ cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj
   return cudaGetLastError();
 }
 
-}  // namespace og
-
-// ---- allocation-free entry point ----------------------------------------------------------
-// og_sssp_delta_noalloc runs the same round-synchronous kernel as og_sssp_delta, but its
-// scratch (query cursor, barrier words, counters, bucket ring and overflow pile) lives in
-// the fixed device array below instead of memory the library allocates.  It serves
-// callers that cannot call cudaMalloc: code inside a host application whose allocator has
-// already claimed the device memory, code on a path where cudaMalloc's implicit device
-// synchronisation is not acceptable, and code that must not meet an out-of-memory error
-// after start-up.  The array is reserved on every GPU that loads the library, for the
-// life of the process.
-#include <mutex>
-
-#include "og.h"
-
-namespace og {
-
-constexpr size_t kNoAllocBytes = 64ull << 20;           // scratch array size (64 MiB)
-constexpr uint32_t kNoAllocMaxN = 1u << 20;             // largest graph accepted
-constexpr size_t kNoAllocHeader = 4096;                 // state words before the arena
-constexpr int kNoAllocMaxDevices = 64;
-
-static __device__ __align__(256) unsigned char og_noalloc_scratch[kNoAllocBytes];
-
-namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-int g_noalloc_occ[kNoAllocMaxDevices] = {};
-int g_noalloc_sms[kNoAllocMaxDevices] = {};
-}  // namespace
-
-}  // namespace og
-
-extern "C" int og_sssp_delta_noalloc(const uint32_t* offsets, const uint32_t* edges, uint32_t n,
-                                     uint64_t m, uint32_t src, uint32_t delta,
-                                     uint32_t* dist_out, void* stream) {
-  using namespace og;
-  if (!offsets || !dist_out || (m && !edges) || n == 0 || src >= n || delta == 0)
-    return OG_E_INVALID;
-  if (n > kNoAllocMaxN || m >= 0xFFFFFFFFull) return OG_E_INVALID;
-  cudaStream_t st = (cudaStream_t)stream;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
-    cudaGetLastError();
-    return OG_E_CUDA;
+// Checks a caller's device CSR before any kernel walks it: offsets[0] = 0, offsets[n] = m,
+// offsets non-decreasing (flags[0] bit 0) and every neighbor < n (bit 1).  Reads only
+// offsets[0 .. n] and the m {neighbor, weight} pairs, so a malformed graph is reported
+// instead of being followed.
+extern "C" __global__ void og_check_csr_kernel(const uint32_t* off, const uint2* adj, uint32_t n,
+                                               uint32_t m, uint32_t* flags) {
+  uint32_t bad = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)n; i += stride) {
+    const uint32_t a = off[i], b = off[i + 1];
+    if (a > b) bad |= 1u;
+    if (i == 0 && a != 0u) bad |= 1u;
+    if (i + 1 == n && b != m) bad |= 1u;
   }
-  const size_t smem = 2 * (size_t)2048 * (sizeof(uint2) + sizeof(uint16_t));
-  void* base = nullptr;
-  {
-    // Set-up, once per device with that device current: the device address of the array
-    // (host code only ever sees a host-side stand-in for the symbol).
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, og_noalloc_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return OG_E_CUDA;
-      }
-      int occ = 0, sms = 0;
-      if (delta_occupancy(&occ, smem, false) != cudaSuccess || occ < 1 ||
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return OG_E_CUDA;
-      }
-      g_noalloc_occ[dev] = occ;
-      g_noalloc_sms[dev] = sms;
-      g_noalloc_ptr[dev] = p;
-    }
-    base = g_noalloc_ptr[dev];
-  }
-  unsigned char* b = static_cast<unsigned char*>(base);
-  // Header: Sync | Stats | QDesc | QState | frontier prefix | ring counters.
-  Sync* sync = reinterpret_cast<Sync*>(b);
-  Stats* stats = reinterpret_cast<Stats*>(b + 256);
-  QDesc* qd = reinterpret_cast<QDesc*>(b + 512);
-  QState* qs = reinterpret_cast<QState*>(b + 768);
-  uint32_t* pref = reinterpret_cast<uint32_t*>(b + 1024);
-  uint32_t* counts = reinterpret_cast<uint32_t*>(b + 2048);
-  uint32_t max_w = 0xFFFFFFFFu;  // unknown without a pass over the edges: widest ring
-  uint32_t B = kMaxRing;
-  if (delta >= max_w / 2) B = 2;
-  const uint64_t arena = (kNoAllocBytes - kNoAllocHeader) / sizeof(uint2);
-  const uint32_t cap = (uint32_t)(arena / 2 / B);
-  const uint32_t ocap = (uint32_t)(arena / 4);
-  uint2* ring = reinterpret_cast<uint2*>(b + kNoAllocHeader);
-  uint2* ovf = ring + (size_t)B * cap;
-
-  QDesc hq;
-  memset(&hq, 0, sizeof(hq));
-  hq.src = src;
-  hq.dst = kNone;
-  hq.delta = delta;
-  hq.kind = kSSSP;
-  Params P{};
-  P.off = offsets;
-  P.adj = reinterpret_cast<const uint2*>(edges);
-  P.xy = nullptr;
-  P.n = n;
-  P.dist = dist_out;
-  P.qd = qd;
-  P.qs = qs;
-  P.ring = ring;
-  P.counts = counts;
-  P.ovf = ovf;
-  P.fr_pref = pref;
-  P.sync = sync;
-  P.stats = stats;
-  P.nq = 1;
-  P.B = B;
-  P.Bmask = B - 1;
-  P.cap = cap;
-  P.ocap = ocap;
-  P.T = 1024;
-  P.tile = 128;
-  P.bin_cap = 2048;
-  P.max_rounds = 0xFFFFFFFFu;
-  P.has_astar = 0;
-  P.spin_ns = 2000000000ull;
-  // Calls share the array: the state words start from zero on every call (two calls
-  // that overlap on the GPU would race on it).
-  if (cudaMemsetAsync(b, 0, kNoAllocHeader, st) != cudaSuccess ||
-      cudaMemcpyAsync(qd, &hq, sizeof(hq), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      launch_fill(dist_out, n, nullptr, 1, g_noalloc_sms[dev], st) != cudaSuccess ||
-      launch_init(P, nullptr, 1, st) != cudaSuccess ||
-      launch_delta(P, g_noalloc_sms[dev] * g_noalloc_occ[dev], smem, st) != cudaSuccess) {
-    cudaGetLastError();
-    return OG_E_CUDA;
-  }
-  Sync hs;
-  QState hqs;
-  if (cudaMemcpyAsync(&hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(&hqs, qs, sizeof(hqs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    cudaGetLastError();
-    return OG_E_CUDA;
-  }
-  if (hs.err & kErrTimeout) return OG_E_TIMEOUT;
-  if (hqs.aborted) return OG_E_ARENA;
-  if (hs.err & kErrSat) return OG_E_OVERFLOW;
-  return OG_OK;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)m; i += stride)
+    if (adj[i].x >= n) bad |= 2u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(FULL, bad, o);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(flags, bad);
 }
+
+cudaError_t launch_check_csr(const uint32_t* off, const uint2* adj, uint32_t n, uint32_t m,
+                             uint32_t* flags, int sms, cudaStream_t st) {
+  og_check_csr_kernel<<<sms * 4, 256, 0, st>>>(off, adj, n, m, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace og

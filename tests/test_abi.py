@@ -95,3 +95,24 @@ def test_null_arguments_are_rejected_before_any_device_call(og):
     assert L.og_setcover(fake, 1000001, None, None, out, None, None) == og.E_INVALID
     assert L.og_setcover(fake, 10000, None, None, None, None, None) == og.E_INVALID
     assert L.og_kcore(fake, 7, None, out, None, None) == og.E_INVALID
+
+
+def test_launch_status_mapping_on_hand_built_error_words(og):
+    """Every round-engine entry point maps its launch's error word through one function
+    (og_launch_status); its precedence is checked here on hand-built words."""
+    T, A, S, B = 1, 2, 4, 8  # timeout, arena, saturation, failed bounds check
+    assert og.launch_status(0) == og.OK
+    assert og.launch_status(S) == og.E_OVERFLOW
+    assert og.launch_status(T) == og.E_TIMEOUT
+    assert og.launch_status(T | S) == og.E_TIMEOUT
+    assert og.launch_status(0, arena_out=True) == og.E_ARENA
+    assert og.launch_status(S, arena_out=True) == og.E_ARENA
+    assert og.launch_status(T, arena_out=True) == og.E_TIMEOUT
+    # the arena bit alone is not an error: the caller decides whether the arena can grow
+    assert og.launch_status(A) == og.OK
+    for extra in (0, T, A, S, T | A | S):
+        assert og.launch_status(B | extra, 41, 7, 3, arena_out=bool(extra & A)) == og.E_INTERNAL
+    assert og.launch_status(B, 41, 123, 5) == og.E_INTERNAL
+    assert og.last_cuda_error() == "check 41 failed: value 123, context 5"
+    assert og.launch_status(T) == og.E_TIMEOUT
+    assert og.last_cuda_error() == "grid barrier wait gave up"
