@@ -57,7 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="road-sssp",
                    choices=["road-sssp", "rmat-wbfs", "rmat-sssp", "batch", "serve", "road-bf",
-                            "rmat-kcore", "road-lazy", "rmat-lazy", "rmat-setcover"])
+                            "rmat-kcore", "road-lazy", "rmat-lazy", "rmat-setcover",
+                            "latency"])
     p.add_argument("--side", type=int, default=4900, help="road-like grid side")
     p.add_argument("--scale", type=int, default=24, help="R-MAT scale")
     p.add_argument("--sources", type=int, default=8)
@@ -80,6 +81,10 @@ def parse_args(argv=None):
     p.add_argument("--serve-fusion", type=int, default=64, help="serve: fusion threshold")
     p.add_argument("--sequential", type=int, default=2000,
                    help="serve: queries in the one-at-a-time baseline")
+    p.add_argument("--no-batch", action="store_true",
+                   help="default workload: skip the 256-query batch measurement")
+    p.add_argument("--launch-check", action="store_true",
+                   help="only start the ranks and count them over gloo (no GPU work)")
     return p.parse_args(argv)
 
 
@@ -289,7 +294,8 @@ def run_ours(args):
     nq = len(queries)
     dbuf = torch.empty(nq * g.n, dtype=torch.int32, device=device)
 
-    # m_r per source, from one verified run
+    # m_r per source, from the first run (certified against the oracle's certificate in
+    # the CPU-baseline leg below, outside every timed region)
     _, _, st0 = og.batch_run(G, queries, cfg=cfg, out=dbuf)
     dh = dbuf.cpu().numpy().view(np.uint32).reshape(nq, g.n)
     mr_nr = [reached_edges(g, dh[i]) for i in range(nq)]
@@ -374,9 +380,31 @@ def run_ours(args):
                    "relax": int(best.relax),
                    "speedup_ordered": round(kernel_s * 1e9 / best.kernel_ns, 2)}
 
+    # one source per launch (the same sources and schedule, each its own og_batch_run):
+    # the per-source figure beside the 8-source launch
+    single = None
+    if args.workload == "road-sssp" and nq > 1:
+        one = torch.empty(g.n, dtype=torch.int32, device=device)
+        og.batch_run(G, queries[:1], cfg=cfg, out=one)
+        t_ns = 0
+        for q in queries:
+            _, _, s1 = og.batch_run(G, [q], cfg=cfg, out=one)
+            t_ns += s1.kernel_ns
+        single = {"value": round(m_r / (t_ns / 1e9) / 1e9, 4), "unit": "GTEPS",
+                  "ms_per_source": round(t_ns / 1e6 / nq, 3),
+                  "note": "each source alone in its own launch, same schedule; device time"}
+
+    batch4 = None
+    if args.workload == "road-sssp" and not args.no_batch and world == 1:
+        batch4 = batch_measure(args, with_cpu=not args.no_cpu_baseline)
+
     cpu = None
+    certified = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(g, srcs[:args.cpu_sources], kind)
+        import oracle
+        certified = all(oracle.check_sssp(g, int(srcs[i]), dh[i]) == (0, 0)
+                        for i in range(nq))
 
     if rank == 0:
         value = m_r * world / step_s / 1e9
@@ -413,6 +441,15 @@ def run_ours(args):
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "stats_per_step": {k: v // args.steps for k, v in agg.items()},
         }
+        line["certified_vs_oracle"] = certified
+        if single is not None:
+            line["one_source_per_launch"] = single
+        if batch4 is not None:
+            line["batch_1024"] = {k: batch4[k] for k in (
+                "value", "unit", "one_at_a_time", "exact_batched_eq_alone_eq_oracle",
+                "roofline")}
+            line["batch_1024"]["ms_per_launch"] = batch4["ms_per_step"]
+            line["batch_1024"]["workload"] = batch4["config"]["workload"]
         if ordered is not None:
             line["ordered"] = ordered
         if eager is not None:
@@ -557,9 +594,14 @@ def _oracle_parallel(g, queries, threads: int):
 
 
 def run_batch(args):
+    print(json.dumps(batch_measure(args, with_cpu=True)), flush=True)
+
+
+def batch_measure(args, with_cpu: bool = True) -> dict:
     """256 concurrent queries on the road-like 1024 x 1024 grid: 128 SSSP + 128 PPSP with
     targets 10..1000 grid steps away, one persistent launch per step; compared with the
-    same queries run one launch at a time and with the oracle on the host cores."""
+    same queries run one launch at a time and (CPU-baseline leg) with the oracle on the
+    host cores."""
     import torch
     import graphgen
     import paper_1911_07260_gb300 as og
@@ -592,24 +634,44 @@ def run_batch(args):
         batch_s = (time.perf_counter() - t0) / args.steps
     clocks = clk.summary()
     kernel_s = kernel_ns / 1e9 / args.steps
-    # one launch per query, same schedule, same results
-    one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    # one launch per query, same queries, each SSSP row kept on the device; the results
+    # are compared with the batch only after the timed loop
+    n_sssp = sum(1 for q in queries if q[0] == og.Q_SSSP)
+    rows = torch.empty(n_sssp * g.n, dtype=torch.int32, device="cuda")
+    d_single = np.zeros(nq, np.uint32)
+    og.query_run(G, queries[0][0], queries[0][1], queries[0][2], 0, cfg=cfg1,
+                 out=rows[:g.n])  # warm-up
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    exact = True
+    r = 0
     for i, (kind, s, t, _) in enumerate(queries):
-        out, d, _ = og.query_run(G, kind, s, t, 0, cfg=cfg1, out=one if kind == og.Q_SSSP else None)
         if kind == og.Q_SSSP:
-            exact &= bool(np.array_equal(one.cpu().numpy().view(np.uint32), dist_b[i]))
+            og.query_run(G, kind, s, t, 0, cfg=cfg1, out=rows[r * g.n:(r + 1) * g.n])
+            r += 1
         else:
-            exact &= int(d) == int(d_batch[i])
+            _, d, _ = og.query_run(G, kind, s, t, 0, cfg=cfg1, out=None)
+            d_single[i] = d
+    torch.cuda.synchronize()
     single_s = time.perf_counter() - t0
+    exact = True
+    rows_h = rows.cpu().numpy().view(np.uint32).reshape(n_sssp, g.n)
+    r = 0
+    for i, (kind, s, t, _) in enumerate(queries):
+        if kind == og.Q_SSSP:
+            exact &= bool(np.array_equal(rows_h[r], dist_b[i]))
+            r += 1
+        else:
+            exact &= int(d_single[i]) == int(d_batch[i])
     threads = os.cpu_count() or 1
     sample = [("sssp", int(s), 0) for s in srcs[:16]] + [("ppsp", int(a), int(b)) for a, b in pairs[:16]]
-    cpu_s, cpu_res = _oracle_parallel(g, sample, threads)
-    for (kind, s, t), r in zip(sample, cpu_res):
-        i = [int(x) for x in srcs[:16]].index(s) if kind == "sssp" else 128 + [
-            (int(a), int(b)) for a, b in pairs[:16]].index((s, t))
-        exact &= bool(np.array_equal(r, dist_b[i])) if kind == "sssp" else int(r) == int(d_batch[i])
+    cpu_s = None
+    if with_cpu:
+        cpu_s, cpu_res = _oracle_parallel(g, sample, threads)
+        for (kind, s, t), r in zip(sample, cpu_res):
+            i = [int(x) for x in srcs[:16]].index(s) if kind == "sssp" else 128 + [
+                (int(a), int(b)) for a, b in pairs[:16]].index((s, t))
+            exact &= bool(np.array_equal(r, dist_b[i])) if kind == "sssp" else \
+                int(r) == int(d_batch[i])
     host = torch.empty(nq * g.n, dtype=torch.int32, pin_memory=True)
     og.batch_run(G, queries, cfg=cfg, out=host.numpy())
     t0 = time.perf_counter()
@@ -640,16 +702,17 @@ def run_batch(args):
                      "peak": peak, "unit": "GB/s",
                      "frac": round(bytes_step / kernel_s / 1e9 / peak, 4), "traffic": None,
                      "peak_source": peak_kind, "kernel_ms": round(kernel_s * 1e3, 3)},
-        "cpu_baseline": {"value": round(len(sample) / cpu_s, 2), "unit": "queries/s",
-                         "cores": threads, "kind": "oracle",
-                         "sample": f"{len(sample)} of the queries (16 SSSP + 16 PPSP), "
-                                   f"{threads} host threads, {cpu_s:.1f} s"},
+        "cpu_baseline": None if cpu_s is None else {
+            "value": round(len(sample) / cpu_s, 2), "unit": "queries/s", "cores": threads,
+            "kind": "oracle", "sample": f"{len(sample)} of the queries (16 SSSP + 16 PPSP), "
+                                        f"{threads} host threads, {cpu_s:.1f} s"},
         "e2e": {"value": round(nq / e2e_s, 2), "unit": "queries/s", "h2d_bytes_per_step": 16 * nq,
                 "d2h_bytes_per_step": 4 * nq * g.n},
         "gpu_launches": 3 * args.steps,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
-    print(json.dumps(line), flush=True)
+    G.free()
+    return line
 
 
 def run_serve(args):
@@ -958,8 +1021,79 @@ def run_setcover(args):
     print(json.dumps(line), flush=True)
 
 
+def probe_latency(og, ctas: int, threads: int) -> dict:
+    """Measured round-trip times (ns per dependent access) of the memory operations a
+    fused level waits on: a relaxed load served by L2 and an atomicMin whose result is
+    used, on an 8 MiB array (L2-resident) and a 4 GiB one (mostly HBM), with one warp
+    (unloaded) and with ctas x threads chains in flight (the persistent kernel's
+    occupancy)."""
+    out = {}
+    for size_name, nbytes in (("l2_8MiB", 8 << 20), ("hbm_4GiB", 4 << 30)):
+        for mode_name, mode in (("load", 0), ("atomic", 1)):
+            out[f"{mode_name}_{size_name}_1warp"] = round(og.probe_chain(mode, nbytes, 1, 32, 2000), 1)
+            out[f"{mode_name}_{size_name}_loaded"] = round(
+                og.probe_chain(mode, nbytes, ctas, threads, 200), 1)
+    return out
+
+
+def run_latency(args):
+    """The memory round-trip probe alone (ns per dependent access; lower is better)."""
+    import torch
+    import paper_1911_07260_gb300 as og
+    torch.cuda.init()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ctas, threads = sms * 3, 256
+    with ClockSampler(0) as clk:
+        lat = probe_latency(og, ctas, threads)
+    clocks = clk.summary()
+    line = {"metric": "memory round trip, ns per dependent access", "value":
+            lat["atomic_l2_8MiB_loaded"], "unit": "ns", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": False, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"dependent chains: {ctas} CTAs x {threads} threads "
+                                   "(loaded) or one warp", "hops_loaded": 200,
+                       "hops_1warp": 2000},
+            "latency_ns": lat, "gpu_launches": 16,
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
+    print(json.dumps(line), flush=True)
+
+
+def relaunch_ranks(args, argv) -> int:
+    """--gpus N > 1 without a torchrun environment: start N ranks of this script under
+    torch.distributed.run (one process per GPU, rendezvous on 127.0.0.1) and return
+    their exit status."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={args.gpus}", "--master-addr", "127.0.0.1",
+           "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def launch_check(args):
+    """Each rank joins a gloo group and the ranks count themselves (CPU only): shows that
+    --gpus N started N ranks."""
+    import torch
+    import torch.distributed as dist
+    rank, world, _ = dist_info()
+    dist.init_process_group("gloo")
+    t = torch.ones(1)
+    dist.all_reduce(t)
+    if rank == 0:
+        print(json.dumps({"launch_check": True, "world_size": world, "ranks_counted": int(t.item()),
+                          "gpus_flag": args.gpus}), flush=True)
+    dist.destroy_process_group()
+
+
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
     args = parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_ranks(args, argv))
+    if args.launch_check:
+        launch_check(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -971,6 +1105,8 @@ def main(argv=None):
         run_setcover(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "latency":
+        run_latency(args)
     else:
         run_ours(args)
 

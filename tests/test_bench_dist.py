@@ -55,3 +55,21 @@ def test_single_rank_helpers_need_no_process_group():
     assert bench.reduce_max(3.5, 1) == 3.5
     bench.barrier(1)
     assert bench.shard_sources(np.arange(8), 0, 1, 8).tolist() == list(range(8))
+
+
+def test_gpus_flag_starts_that_many_ranks():
+    """bench.py --gpus 2 without a torchrun environment starts 2 ranks itself (here they
+    only join a gloo group and count themselves)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2",
+                        "--launch-check"], capture_output=True, text=True, timeout=300,
+                       env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert lines == [{"launch_check": True, "world_size": 2, "ranks_counted": 2,
+                      "gpus_flag": 2}]
