@@ -430,6 +430,8 @@ def run_ours(args):
                        "hub_degree": int(eff.hub_degree),
                        "blocks_per_sm": int(eff.blocks_per_sm),
                        "engine": "async" if int(eff.engine) == 2 else "rounds",
+                       "layout": "ell" if int(eff.layout) == 2 else "csr",
+                       "prefetch": int(eff.prefetch) == 1,
                        "bucket_update": "lazy" if int(eff.bucket_update) == 2 else "eager",
                        "l2": "inputs larger than L2 (graph %.0f MB + dist %.0f MB > 129 MB)"
                              % ((8 * g.m + 4 * g.n) / 1e6, 4 * nq * g.n / 1e6),
@@ -1024,15 +1026,19 @@ def run_setcover(args):
 def probe_latency(og, ctas: int, threads: int) -> dict:
     """Measured round-trip times (ns per dependent access) of the memory operations a
     fused level waits on: a relaxed load served by L2 and an atomicMin whose result is
-    used, on an 8 MiB array (L2-resident) and a 4 GiB one (mostly HBM), with one warp
+    used, on an 8 MiB array (L2-resident), on 8 MiB of lines spread over a 2 GiB array
+    (L2-resident, 1,024 pages of 2 MiB) and on a 4 GiB array (mostly HBM), with one warp
     (unloaded) and with ctas x threads chains in flight (the persistent kernel's
     occupancy)."""
     out = {}
-    for size_name, nbytes in (("l2_8MiB", 8 << 20), ("hbm_4GiB", 4 << 30)):
+    for size_name, nbytes, foot in (("l2_8MiB", 8 << 20, 8 << 20),
+                                    ("l2_8MiB_over_2GiB", 2 << 30, 8 << 20),
+                                    ("hbm_4GiB", 4 << 30, 4 << 30)):
         for mode_name, mode in (("load", 0), ("atomic", 1)):
-            out[f"{mode_name}_{size_name}_1warp"] = round(og.probe_chain(mode, nbytes, 1, 32, 2000), 1)
+            out[f"{mode_name}_{size_name}_1warp"] = round(
+                og.probe_chain(mode, nbytes, 1, 32, 2000, foot), 1)
             out[f"{mode_name}_{size_name}_loaded"] = round(
-                og.probe_chain(mode, nbytes, ctas, threads, 200), 1)
+                og.probe_chain(mode, nbytes, ctas, threads, 200, foot), 1)
     return out
 
 
@@ -1052,7 +1058,7 @@ def run_latency(args):
             "config": {"workload": f"dependent chains: {ctas} CTAs x {threads} threads "
                                    "(loaded) or one warp", "hops_loaded": 200,
                        "hops_1warp": 2000},
-            "latency_ns": lat, "gpu_launches": 16,
+            "latency_ns": lat, "gpu_launches": 24,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
     print(json.dumps(line), flush=True)
 

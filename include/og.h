@@ -85,7 +85,8 @@ typedef struct og_config {
   uint32_t layout;           /* adjacency read by the kernels: OG_LAYOUT_CSR, or
                                 OG_LAYOUT_ELL (one 64-byte row of up to 8 edges per
                                 vertex, built at upload when every degree is <= 8;
-                                0 = CSR)                                               */
+                                0 = ELL where the rows exist, else CSR; the server
+                                defaults to CSR)                                       */
   uint32_t prefetch;         /* OG_PREFETCH_ON / _OFF: prefetch an inserted vertex's
                                 adjacency into L2 (0 = off)                           */
   uint32_t hub_degree;       /* out-degree from which a frontier vertex is a hub: instead
@@ -373,14 +374,17 @@ int og_launch_status(uint32_t err, uint32_t bad_code, uint32_t bad_val, uint32_t
                      uint32_t arena_out);
 /* Memory round-trip probe (a measurement aid; the paper has no counterpart): ctas x
  * threads threads each follow a chain of hops dependent accesses through a fresh
- * device array of bytes bytes (a power of two, 4 KiB .. 16 GiB; every hop lands far
- * from the previous one), and *ns_per_hop receives the kernel time / hops, i.e. the
- * round-trip time of one access with that many chains in flight.  mode 0: relaxed loads
- * served by L2; 1: atomicMin whose result is used (the array is left unchanged); 2:
- * non-coherent loads through L1.  Allocates and frees its array; synchronises the
- * device.  OG_E_INVALID for bad sizes (threads a multiple of 32, at most 1024). */
-int og_probe_chain(uint32_t mode, uint64_t bytes, uint32_t ctas, uint32_t threads,
-                   uint32_t hops, double* ns_per_hop);
+ * device array of bytes bytes (a power of two, 4 KiB .. 16 GiB).  The chains visit
+ * footprint / 128 lines of 128 bytes spread evenly over the array (footprint a power of
+ * two, 4 KiB .. bytes; every hop lands far from the previous one): footprint = bytes
+ * touches the whole array, a small footprint spread over a large array stays in L2 but
+ * spans many pages.  *ns_per_hop receives the kernel time / hops, i.e. the round-trip
+ * time of one access with that many chains in flight.  mode 0: relaxed loads served by
+ * L2; 1: atomicMin whose result is used (the array is left unchanged); 2: non-coherent
+ * loads through L1.  Allocates and frees its array; synchronises the device.
+ * OG_E_INVALID for bad sizes (threads a multiple of 32, at most 1024). */
+int og_probe_chain(uint32_t mode, uint64_t bytes, uint64_t footprint, uint32_t ctas,
+                   uint32_t threads, uint32_t hops, double* ns_per_hop);
 const char* og_strerror(int code);
 const char* og_last_cuda_error(void);
 int og_version(void);

@@ -111,7 +111,7 @@ def lib():
             "og_version": (i32, []),
             "og_sssp_delta_noalloc": (i32, [vp, vp, u32, u64, u32, u32, vp, vp]),
             "og_launch_status": (i32, [u32, u32, u32, u32, u32]),
-            "og_probe_chain": (i32, [u32, u64, u32, u32, u32, P(ctypes.c_double)]),
+            "og_probe_chain": (i32, [u32, u64, u64, u32, u32, u32, P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -424,11 +424,14 @@ def launch_status(err: int, bad_code: int = 0, bad_val: int = 0, bad_aux: int = 
     return int(lib().og_launch_status(err, bad_code, bad_val, bad_aux, 1 if arena_out else 0))
 
 
-def probe_chain(mode: int, nbytes: int, ctas: int, threads: int, hops: int) -> float:
-    """ns per dependent access: mode 0 L2 loads, 1 atomicMin round trips, 2 L1 loads."""
+def probe_chain(mode: int, nbytes: int, ctas: int, threads: int, hops: int,
+                footprint: int = 0) -> float:
+    """ns per dependent access: mode 0 L2 loads, 1 atomicMin round trips, 2 L1 loads;
+    footprint (default: the whole array) = bytes of 128-byte lines the chains visit,
+    spread evenly over the nbytes array."""
     v = ctypes.c_double(0.0)
-    _check(lib().og_probe_chain(mode, nbytes, ctas, threads, hops, ctypes.byref(v)),
-           "og_probe_chain")
+    _check(lib().og_probe_chain(mode, nbytes, footprint or nbytes, ctas, threads, hops,
+                                ctypes.byref(v)), "og_probe_chain")
     return float(v.value)
 
 

@@ -38,6 +38,8 @@ cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t s
 cudaError_t async_occupancy(int* blocks_per_sm, size_t smem, bool ell);
 cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,
                               cudaStream_t st);
+cudaError_t launch_touch_reset(uint32_t* dist, uint32_t n, uint32_t* touched, uint32_t tb_words,
+                               const uint32_t* slots, uint32_t nslots, int sms, cudaStream_t st);
 cudaError_t kcore_occupancy(int* blocks_per_sm);
 cudaError_t launch_kcore(const KParams& P, int grid, cudaStream_t st);
 cudaError_t launch_kcore_init(const uint32_t* off, uint32_t* prio, uint32_t n, int sms,
@@ -140,6 +142,7 @@ struct HBuf {
 // Device scratch of one launch configuration (grown on demand, reused across calls).
 struct Workspace {
   DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big, bmap;
+  DBuf stouched;  // server: touched-block bitmaps of the slots' distance rows
   DBuf kprio, kcnt, ktouched, klist, kring, kcounts, klossy, kstate;  // k-core
   DBuf lzbits, lzlist;  // lazy bucket update
   DBuf sclad, sclen, scpk, sccov, scclaim, scseen, scmeta, scbase, scbl, scsm, sclg, scstate,
@@ -153,7 +156,7 @@ struct Workspace {
   void* ring_ptr = nullptr;
   void release() {
     for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
-                    &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
+                    &stouched, &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
                     &kstate, &lzbits, &lzlist, &sclad, &sclen, &scpk, &sccov, &scclaim, &scseen,
                     &scmeta, &scbase, &scbl, &scsm, &sclg, &scstate, &scpri, &scout})
       b->release();
@@ -283,7 +286,9 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.engine = u.engine ? u.engine : g->cfg.engine;
   r.precheck = u.precheck ? u.precheck : g->cfg.precheck;
   r.layout = u.layout ? u.layout : g->cfg.layout;
-  if (!r.layout) r.layout = OG_LAYOUT_CSR;  // measured faster than ELL on road graphs
+  // Graphs of degree <= 8 have ELL rows: the round engine's row path (two dependent
+  // round trips per fused level instead of three) measured faster than CSR on them.
+  if (!r.layout) r.layout = g->ell ? OG_LAYOUT_ELL : OG_LAYOUT_CSR;
   r.prefetch = u.prefetch ? u.prefetch : (g->cfg.prefetch ? g->cfg.prefetch : OG_PREFETCH_OFF);
   if (!r.layout || (r.layout == OG_LAYOUT_ELL && !g->ell))
     r.layout = g->ell ? OG_LAYOUT_ELL : OG_LAYOUT_CSR;
@@ -1255,6 +1260,8 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   if (!s) return OG_E_OOM;
   s->g = g;
   s->cfg = resolve(g, cfg);
+  // The server's barrier-free engine keeps CSR unless a layout is asked for explicitly.
+  if (!(cfg && cfg->layout) && !g->cfg.layout) s->cfg.layout = OG_LAYOUT_CSR;
   if (s->cfg.bucket_update == OG_UPDATE_LAZY) {  // the server runs the barrier-free engine
     delete s;
     return OG_E_INVALID;
@@ -1287,7 +1294,9 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   s->ocap = (uint32_t)std::max<uint64_t>(64, entries / 4);
   Workspace& ws = s->ws;
   int r = OG_OK;
+  const uint32_t tbw = touch_words(g->n);
   if (r == OG_OK) r = ws.dist.ensure(sizeof(uint32_t) * (size_t)slots * g->n);
+  if (r == OG_OK) r = ws.stouched.ensure(sizeof(uint32_t) * (size_t)slots * tbw);
   if (r == OG_OK) r = ws.ring.ensure(sizeof(uint2) * (size_t)slots * B * s->cap);
   if (r == OG_OK) r = ws.counts.ensure(sizeof(uint32_t) * (size_t)slots * B);
   if (r == OG_OK) r = ws.ovf.ensure(sizeof(uint2) * (size_t)slots * 2 * s->ocap);
@@ -1313,6 +1322,21 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
     r = OG_E_CUDA;
   if (r == OG_OK && cudaMemsetAsync(ws.sync.p, 0, sizeof(Sync), s->stream) != cudaSuccess)
     r = OG_E_CUDA;
+  // Every slot's distance row starts unreachable, once: afterwards a slot is reset only
+  // in the blocks its last query reached (touched bitmap), when a new query is admitted.
+  if (r == OG_OK && cudaMemsetAsync(ws.stouched.p, 0, sizeof(uint32_t) * (size_t)slots * tbw,
+                                    s->stream) != cudaSuccess)
+    r = OG_E_CUDA;
+  if (r == OG_OK) {
+    int dev = 0;
+    if (!g->sms && (cudaGetDevice(&dev) != cudaSuccess ||
+                    cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                        cudaSuccess))
+      r = OG_E_CUDA;
+    else if (launch_fill(ws.dist.as<uint32_t>(), g->n, nullptr, slots, g->sms, s->stream) !=
+             cudaSuccess)
+      r = OG_E_CUDA;
+  }
   if (r == OG_OK) r = clean_ring(ws, (uint64_t)slots * B * s->cap, s->stream);
   if (r == OG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = OG_E_CUDA;
   if (r != OG_OK) {
@@ -1365,6 +1389,8 @@ int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active) {
   AParams P = async_params(g, ws, ws.dist.as<uint32_t>(), s->slots, s->B, s->cap, s->ocap,
                            s->cfg, astar);
   P.budget_ns = (unsigned long long)budget_us * 1000ull;
+  P.touched = ws.stouched.as<uint32_t>();
+  P.tb_words = touch_words(g->n);
   const uint32_t np = (uint32_t)s->pending.size();
   if (np) {
     QDesc* hqd = ws.h_qd.as<QDesc>();
@@ -1373,7 +1399,10 @@ int og_server_step(og_server* s, uint32_t budget_us, uint32_t* n_active) {
     CK(cudaMemcpyAsync(ws.qd.p, hqd, sizeof(QDesc) * s->slots, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ws.slots.p, ws.h_slots.p, sizeof(uint32_t) * np,
                        cudaMemcpyHostToDevice, st));
-    CK(launch_fill(P.dist, g->n, ws.slots.as<uint32_t>(), np, g->sms, st));
+    // Admitted slots: back to unreachable where the previous query reached (O(touched),
+    // not O(n)), then started.
+    CK(launch_touch_reset(P.dist, g->n, P.touched, P.tb_words, ws.slots.as<uint32_t>(), np,
+                          g->sms, st));
     CK(launch_async_init(P, ws.slots.as<uint32_t>(), np, st));
     for (uint32_t slot : s->pending) s->state[slot] = 2;
     s->pending.clear();

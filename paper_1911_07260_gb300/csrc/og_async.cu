@@ -160,6 +160,17 @@ __device__ __forceinline__ uint32_t relax_edges_async(const AParams& P, WarpQ& L
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) old[k] = go[k] ? atomicMin(dq + ew[k].x, nd[k]) : 0u;
+  if (P.touched) {
+    // First reach of a vertex (its distance was unreachable): mark its block, so the
+    // slot's row can later be reset block by block (the result is not waited for).
+    uint32_t* tb = P.touched + (size_t)L.q * P.tb_words;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (go[k] && old[k] == kInf) {
+        const uint32_t b = ew[k].x >> kTouchShift;
+        atomicOr(tb + (b >> 5), 1u << (b & 31u));
+      }
+  }
   uint32_t added = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -752,6 +763,10 @@ extern "C" __global__ void og_async_init_kernel(AParams P, const uint32_t* slots
   const uint32_t q = slots ? slots[t] : t;
   const QDesc d = P.qd[q];
   P.dist[(size_t)q * P.n + d.src] = 0u;
+  if (P.touched) {
+    const uint32_t b = d.src >> kTouchShift;
+    atomicOr(P.touched + (size_t)q * P.tb_words + (b >> 5), 1u << (b & 31u));
+  }
   const uint32_t h0 = d.kind == kASTAR ? heuristic(P.xy, P.xy_integral, d.src, d.tx, d.ty) : 0u;
   const uint32_t key0 = bucket_of(0u, h0, d.delta);
   uint32_t* cnts = P.counts + (size_t)q * P.B;
@@ -781,6 +796,54 @@ extern "C" __global__ void og_async_init_kernel(AParams P, const uint32_t* slots
   P.aq[q] = s;
   __threadfence();
   atomicAdd(&P.sync->active, 1u);
+}
+
+// Resets the distance rows of the listed slots to unreachable, only in the blocks their
+// touched bitmaps mark, and clears those bitmaps (blockIdx.y indexes the slot list).  A
+// warp takes one bitmap word at a time and fills each marked block of kTouchBlock
+// vertices with 16-byte stores.
+extern "C" __global__ void og_touch_reset_kernel(uint32_t* dist, uint32_t n, uint32_t* touched,
+                                                 uint32_t tb_words, const uint32_t* slots) {
+  const uint32_t q = slots[blockIdx.y];
+  uint32_t* d = dist + (size_t)q * n;
+  uint32_t* tb = touched + (size_t)q * tb_words;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t wpb = blockDim.x >> 5;
+  for (uint32_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < tb_words; i += gridDim.x * wpb) {
+    uint32_t word = 0;
+    if (lane == 0) {
+      word = tb[i];
+      if (word) tb[i] = 0u;
+    }
+    word = __shfl_sync(FULL, word, 0);
+    while (word) {
+      const uint32_t bit = (uint32_t)(__ffs(word) - 1);
+      word &= word - 1u;
+      const size_t v0 = ((size_t)i * 32u + bit) << kTouchShift;
+      // kTouchBlock = 256 vertices: 8 per lane, in two 16-byte stores when the block is
+      // whole and 16-byte aligned, else word by word.
+      const size_t end = min((size_t)n, v0 + kTouchBlock);
+      const bool vec = end == v0 + kTouchBlock && (((uintptr_t)(d + v0)) & 15u) == 0;
+      if (vec) {
+        uint4* p = reinterpret_cast<uint4*>(d + v0);
+        p[lane] = make_uint4(kInf, kInf, kInf, kInf);
+        p[lane + 32] = make_uint4(kInf, kInf, kInf, kInf);
+      } else {
+        for (size_t v = v0 + lane; v < end; v += 32) d[v] = kInf;
+      }
+    }
+  }
+}
+
+cudaError_t launch_touch_reset(uint32_t* dist, uint32_t n, uint32_t* touched, uint32_t tb_words,
+                               const uint32_t* slots, uint32_t nslots, int sms, cudaStream_t st) {
+  if (nslots == 0) return cudaSuccess;
+  uint32_t gx = (tb_words + 7u) / 8u;
+  const uint32_t cap = (uint32_t)sms * 2u;
+  if (gx > cap) gx = cap;
+  if (gx < 1) gx = 1;
+  og_touch_reset_kernel<<<dim3(gx, nslots), 256, 0, st>>>(dist, n, touched, tb_words, slots);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t st) {

@@ -197,6 +197,17 @@ struct AParams {
   uint32_t prefetch;
   unsigned long long spin_ns;
   unsigned long long budget_ns;  // stop (resumably) after this long; 0 = run to the end
+  uint32_t* touched;        // nq x tb_words bitmap of kTouchBlock-vertex blocks holding a
+                            // vertex this query reached (server: lets a slot's distance
+                            // row be reset block by block); null = not tracked
+  uint32_t tb_words;
 };
+
+// Granularity of the server's touched-vertex bitmap: one bit per 256 consecutive vertices.
+constexpr uint32_t kTouchShift = 8;
+constexpr uint32_t kTouchBlock = 1u << kTouchShift;
+__host__ __device__ constexpr uint32_t touch_words(uint32_t n) {
+  return (uint32_t)(((uint64_t)n + ((uint64_t)kTouchBlock << 5) - 1) / ((uint64_t)kTouchBlock << 5));
+}
 
 }  // namespace og

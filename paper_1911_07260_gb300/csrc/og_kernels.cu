@@ -408,29 +408,16 @@ __device__ void flush_outbox(const Params& P, Smem& S, const Bins& B, const BinO
   if (threadIdx.x == 0) S.obN = 0;
 }
 
-// Expands the bucket entries held by a warp (one per lane with has) on the ELL layout:
-// the lane reads its vertex's whole row (up to 8 {neighbor, weight} pairs, 64 bytes)
-// together with the stale check, then issues the row's atomicMins, so a level costs
-// two dependent memory round trips.  Improved vertices of the current bucket go to the
-// CTA's bin with one warp-wide scan and one shared-memory atomic; those of later
-// buckets are staged in the outbox.  All 32 lanes.
+// Relaxes one loaded ELL row per lane (lanes with live; g = the row's vertex distance):
+// issues the row's atomicMins, then sends improved vertices of the current bucket to
+// the CTA's bin with one warp-wide scan and one shared-memory atomic, and those of later
+// buckets to the outbox.  All 32 lanes.
 template <bool ASTAR>
-__device__ __forceinline__ void expand_rows(const Params& P, Smem& S, const Bins& B,
-                                            const BinOut& O, bool allow_local, bool has,
-                                            uint32_t u, uint32_t g, uint32_t q, Cnt& C) {
+__device__ __forceinline__ void relax_row(const Params& P, Smem& S, const Bins& B,
+                                          const BinOut& O, bool allow_local, bool live,
+                                          const uint2 (&ew)[kEllWidth], uint32_t g,
+                                          uint32_t q, Cnt& C) {
   const uint32_t lane = threadIdx.x & 31;
-  uint2 ew[kEllWidth];
-  uint32_t d = 0;
-  if (has) {
-    C.items++;
-    d = __ldcg(P.dist + (size_t)q * P.n + u);
-    load_row(P.ell, u, ew);
-  } else {
-#pragma unroll
-    for (int k = 0; k < kEllWidth; ++k) ew[k] = make_uint2(kNone, 0u);
-  }
-  const bool live = has && d == g;
-  if (has && !live) C.stale++;
   uint32_t* dq = P.dist + (size_t)q * P.n;
   unsigned okm = 0;
   uint32_t nd[kEllWidth];
@@ -504,6 +491,29 @@ __device__ __forceinline__ void expand_rows(const Params& P, Smem& S, const Bins
     }
   }
   if (__any_sync(FULL, gm != 0u)) stage_later<ASTAR>(P, S, B, O, gm, ew, nd, q, astar, C);
+}
+
+// Expands the bucket entries held by a warp (one per lane with has) on the ELL layout:
+// the lane reads its vertex's whole row (up to 8 {neighbor, weight} pairs, 64 bytes)
+// together with the stale check, then relaxes it (relax_row), so a level costs two
+// dependent memory round trips.  All 32 lanes.
+template <bool ASTAR>
+__device__ __forceinline__ void expand_rows(const Params& P, Smem& S, const Bins& B,
+                                            const BinOut& O, bool allow_local, bool has,
+                                            uint32_t u, uint32_t g, uint32_t q, Cnt& C) {
+  uint2 ew[kEllWidth];
+  uint32_t d = 0;
+  if (has) {
+    C.items++;
+    d = __ldcg(P.dist + (size_t)q * P.n + u);
+    load_row(P.ell, u, ew);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kEllWidth; ++k) ew[k] = make_uint2(kNone, 0u);
+  }
+  const bool live = has && d == g;
+  if (has && !live) C.stale++;
+  relax_row<ASTAR>(P, S, B, O, allow_local, live, ew, g, q, C);
 }
 
 // Block-wide exclusive scan of a[0..n) in place (each thread scans a run of

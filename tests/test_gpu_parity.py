@@ -644,3 +644,32 @@ def test_server_on_recycled_device_memory(og, orc, gg, road300):
             break
     srv.free()
     assert got == {i: orc.ppsp(g, int(s), int(t)) for i, (s, t) in enumerate(pairs.tolist())}
+
+
+def test_server_slot_reuse_resets_the_reached_blocks(og, orc, gg, road300):
+    """A reused slot is reset only in the 256-vertex blocks its previous query reached
+    (its touched bitmap), not over the whole row: 80 queries through 2 slots, long-reach
+    queries alternating with short ones and SSSP queries that reach every block, every
+    result against the oracle.  A block left unreset would hand a later query a distance
+    below the true one."""
+    g, G = road300
+    pairs = gg.sample_pairs_grid_steps(g, 80, 3, 500, seed=44, log_uniform=True)
+    srv = og.Server(G, max_slots=2, cfg=og.config(delta=256, fusion_threshold=64))
+    got = {}
+    i = 0
+    kinds = {}
+    while len(got) < len(pairs):
+        while i < len(pairs):
+            s, t = pairs[i].tolist()
+            kind = (og.Q_SSSP, og.Q_PPSP, og.Q_ASTAR)[i % 3]
+            if not srv.submit(kind, s, t, tag=i):
+                break
+            kinds[i] = kind
+            i += 1
+        srv.step(budget_us=100)
+        tags, d = srv.poll()
+        got.update({int(a): int(b) for a, b in zip(tags, d)})
+    srv.free()
+    for j, (s, t) in enumerate(pairs.tolist()):
+        if kinds[j] != og.Q_SSSP:
+            assert got[j] == orc.ppsp(g, s, t), (j, kinds[j])
