@@ -286,12 +286,11 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.engine = u.engine ? u.engine : g->cfg.engine;
   r.precheck = u.precheck ? u.precheck : g->cfg.precheck;
   r.layout = u.layout ? u.layout : g->cfg.layout;
-  // Graphs of degree <= 8 have ELL rows: the round engine's row path (two dependent
-  // round trips per fused level instead of three) measured faster than CSR on them.
-  if (!r.layout) r.layout = g->ell ? OG_LAYOUT_ELL : OG_LAYOUT_CSR;
+  // layout 0 stays "automatic": the round engine picks its ELL row path (two dependent
+  // round trips per fused level instead of three, measured faster) on graphs with ELL
+  // rows when no A* query is in the launch, CSR otherwise (run_chunk_rounds).
   r.prefetch = u.prefetch ? u.prefetch : (g->cfg.prefetch ? g->cfg.prefetch : OG_PREFETCH_OFF);
-  if (!r.layout || (r.layout == OG_LAYOUT_ELL && !g->ell))
-    r.layout = g->ell ? OG_LAYOUT_ELL : OG_LAYOUT_CSR;
+  if (r.layout == OG_LAYOUT_ELL && !g->ell) r.layout = OG_LAYOUT_CSR;
   if (!r.precheck)
     r.precheck = (g->n && (double)g->m / g->n > 8.0) ? OG_PRECHECK_ON : OG_PRECHECK_OFF;
   return r;
@@ -351,15 +350,18 @@ struct RunOut {
 int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, const og_config& c,
               uint32_t* dist_dev, uint32_t* d_out, Stats* acc, RunOut* ro, cudaStream_t st) {
   const size_t smem = delta_smem_bytes(kBinCap);
-  // The lazy bucket update marks vertices instead of inserting them: CSR kernel only.
-  const bool ell = c.layout == OG_LAYOUT_ELL && g->ell && c.bucket_update != OG_UPDATE_LAZY;
-  TRY(occupancy(g, smem, ell));
   uint32_t min_delta = 0xFFFFFFFFu;
   bool astar = false;
   for (uint32_t i = 0; i < nq; ++i) {
     if (qd[i].kind != kBF) min_delta = std::min(min_delta, qd[i].delta);  // BF: 2 buckets
     astar |= qd[i].kind == kASTAR;
   }
+  // The lazy bucket update marks vertices instead of inserting them: CSR kernel only.
+  // An automatic layout takes the ELL rows when they exist and no A* query is in the
+  // launch (on ELL rows the A* heuristic costs a dependent load after the atomics).
+  const bool ell = g->ell && c.bucket_update != OG_UPDATE_LAZY &&
+                   (c.layout == OG_LAYOUT_ELL || (c.layout == 0 && !astar));
+  TRY(occupancy(g, smem, ell));
   const uint32_t B = ring_size(g, c, min_delta);
   uint64_t entries = c.arena_entries ? c.arena_entries : default_arena(g, nq);
   TRY(ws.events());
@@ -1260,8 +1262,9 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   if (!s) return OG_E_OOM;
   s->g = g;
   s->cfg = resolve(g, cfg);
-  // The server's barrier-free engine keeps CSR unless a layout is asked for explicitly.
-  if (!(cfg && cfg->layout) && !g->cfg.layout) s->cfg.layout = OG_LAYOUT_CSR;
+  // The server's barrier-free engine runs CSR unless its caller asks for ELL rows (a
+  // layout tuned for the graph's round engine does not carry over).
+  s->cfg.layout = (cfg && cfg->layout == OG_LAYOUT_ELL && g->ell) ? OG_LAYOUT_ELL : OG_LAYOUT_CSR;
   if (s->cfg.bucket_update == OG_UPDATE_LAZY) {  // the server runs the barrier-free engine
     delete s;
     return OG_E_INVALID;
@@ -1602,7 +1605,7 @@ int autotune_queries(og_graph* g, const std::vector<og_query>& qs, uint32_t delt
   // which another tuning call may have changed (a batch then ran with the CTA count
   // tuned for a single query).
   if (!best.blocks_per_sm) {
-    const bool ell = best.layout == OG_LAYOUT_ELL && g->ell;
+    const bool ell = g->ell && (best.layout == OG_LAYOUT_ELL || best.layout == 0);
     const int occ = best.engine == OG_ENGINE_ASYNC ? g->occ_async_l[ell] : g->occ_l[ell];
     if (occ > 0) best.blocks_per_sm = (uint32_t)occ;
   }

@@ -15,7 +15,10 @@
 // marked and its level is rebuilt by a scan (priority == k) instead.
 // One cooperative persistent launch; phases are separated by a bounded grid barrier whose
 // last arriver decides the next phase (kdecide).  The final priorities are the coreness.
+#include <stddef.h>
+
 #include "og_device.cuh"
+
 #include "og_kcore.cuh"
 
 namespace og {
@@ -392,32 +395,39 @@ __device__ __forceinline__ uint32_t kread(const uint32_t* p) {
   if ((threadIdx.x & 31) == 0) v = __ldcg(p);
   return __shfl_sync(FULL, v, 0);
 }
-__device__ __forceinline__ unsigned long long kread64(const unsigned long long* p) {
-  unsigned long long v = 0;
-  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
-  return __shfl_sync(FULL, v, 0);
-}
+
+// The decider's view of KState: lane i loads word i in one round trip (every other CTA
+// has arrived, so no word changes any more), and each field is taken from its lane by a
+// shuffle, so every lane sees the same value.
+constexpr uint32_t kKStateWords = sizeof(KState) / 4;
+static_assert(kKStateWords <= 31 && sizeof(KState) % 8 == 0, "KState and the error word fit one warp load");
+#define KS_WORD(f) ((uint32_t)(offsetof(KState, f) / 4))
 
 // Run by warp 0 of the CTA that arrives last at a grid barrier: the next phase and level.
-// Every value a decision depends on is read warp-uniformly (kread).
+// Every value a decision depends on is warp-uniform: the state block is read once
+// (snapshot) and the bucket arrays through ballots or kread.
 __device__ void kdecide(const KParams& P, uint32_t done) {
   const uint32_t lane = threadIdx.x & 31;
   KState* ks = P.ks;
   Sync* sy = P.sync;
-  const bool fatal = (kread(&sy->err) & kErrFatal) != 0u;
+  const uint32_t snap = lane < kKStateWords ? __ldcg(reinterpret_cast<const uint32_t*>(ks) + lane)
+                                            : (lane == 31 ? ld_relaxed(&sy->err) : 0u);
+  auto F = [&](uint32_t w) -> uint32_t { return __shfl_sync(FULL, snap, (int)w); };
+  const bool fatal = (F(31) & kErrFatal) != 0u;
   uint32_t next = kKStop;
   // Level c of the window: a bucket that overflowed is rebuilt by a scan.
-  // The state words were written by earlier deciders on other SMs: read them from L2.
   auto start_level = [&](uint32_t c) -> uint32_t {
+    const uint32_t base = F(KS_WORD(base)), levels = F(KS_WORD(levels));
+    const uint32_t scans = F(KS_WORD(scans)), asel = F(KS_WORD(asel));
     if (lane == 0) {
       ks->cur = c;
-      ks->k = __ldcg(&ks->base) + c;
-      ks->levels = __ldcg(&ks->levels) + 1u;
+      ks->k = base + c;
+      ks->levels = levels + 1u;
     }
     if (kread(P.lossy + c)) {
       if (lane == 0) {
-        ks->next_n[__ldcg(&ks->asel)] = 0u;
-        ks->scans = __ldcg(&ks->scans) + 1u;
+        ks->next_n[asel] = 0u;
+        ks->scans = scans + 1u;
       }
       return kKScan;
     }
@@ -430,25 +440,26 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
   // The level is done: the next non-empty (or overflowed) bucket of the window, else a
   // refill of the window from the smallest priority above it.
   auto level_done = [&]() -> uint32_t {
-    const uint32_t cur = kread(&ks->cur);
+    const uint32_t cur = F(KS_WORD(cur));
     for (uint32_t c0 = cur + 1; c0 < kKRing; c0 += 32) {
       const uint32_t c = c0 + lane;
       const bool ne = c < kKRing && (__ldcg(P.counts + c) > 0u || __ldcg(P.lossy + c) != 0u);
       const unsigned b = __ballot_sync(FULL, ne);
       if (b) return start_level(c0 + (uint32_t)(__ffs(b) - 1));
     }
+    const uint32_t base = F(KS_WORD(base)), refills = F(KS_WORD(refills));
     if (lane == 0) {  // window exhausted: refill from the smallest priority above it
-      ks->lo = __ldcg(&ks->base) + kKRing;
+      ks->lo = base + kKRing;
       ks->kmin = kInf;
-      ks->refills = __ldcg(&ks->refills) + 1u;
+      ks->refills = refills + 1u;
     }
     return kKMin;
   };
   // Eager: vertices that dropped to k wait in list[asel]; they are the next round.
   auto after_round = [&]() -> uint32_t {
     if (lane == 0) P.stats->v[kStRounds] += 1ull;
-    const uint32_t a = kread(&ks->asel);
-    const uint32_t na = kread(&ks->next_n[a]);
+    const uint32_t a = F(KS_WORD(asel)) & 1u;
+    const uint32_t na = F(KS_WORD(next_n) + a);
     if (na > 0u) {  // vertices dropped to k: another round at this level
       if (lane == 0) {
         ks->fr_list = 1u;
@@ -465,8 +476,8 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
   // extracted) by the next apply phase, which counts into the other list, reset here.
   auto lazy_next = [&]() -> uint32_t {
     if (lane == 0) P.stats->v[kStRounds] += 1ull;
-    const uint32_t t = kread(&ks->tsel);
-    if (kread(&ks->touched_n[t]) > 0u) {
+    const uint32_t t = F(KS_WORD(tsel)) & 1u;
+    if (F(KS_WORD(touched_n) + t) > 0u) {
       if (lane == 0) {
         ks->tsel = t ^ 1u;
         ks->touched_n[t ^ 1u] = 0u;
@@ -485,7 +496,7 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
         next = kKMin;
         break;
       case kKMin: {
-        const uint32_t km = kread(&ks->kmin);
+        const uint32_t km = F(KS_WORD(kmin));
         if (km == kInf) {
           next = kKStop;
         } else {
@@ -501,20 +512,22 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
       case kKFill:
         next = start_level(0u);
         break;
-      case kKScan:
+      case kKScan: {
+        const uint32_t a = F(KS_WORD(asel)) & 1u;
+        const uint32_t na = F(KS_WORD(next_n) + a);
         if (lane == 0) {
-          const uint32_t a = __ldcg(&ks->asel);
           ks->fr_list = 1u;
           ks->fsel = a;
-          ks->fr_n = min(__ldcg(&ks->next_n[a]), P.n);
+          ks->fr_n = min(na, P.n);
           ks->asel = a ^ 1u;
           ks->next_n[a ^ 1u] = 0u;
         }
         next = kKPeel;
         break;
+      }
       case kKPeel:
       case kKApply:
-        if ((kread64(&ks->hub_word) >> 32) > 0u) {  // hubs listed: their edges first
+        if (F(KS_WORD(hub_word) + 1) > 0u) {  // hubs listed (high word): their edges first
           next = kKHub;
           break;
         }
@@ -537,6 +550,7 @@ __device__ void kdecide(const KParams& P, uint32_t done) {
     sy->work = 0u;
   }
 }
+#undef KS_WORD
 
 // Bounded grid barrier (as in the Delta-stepping engine): the last CTA to arrive runs
 // kdecide and releases the others, who give up after spin_ns or on a fatal error.
@@ -572,7 +586,9 @@ __device__ void kbarrier(const KParams& P, KSmem& S, uint32_t& bar, uint32_t don
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    S.phase = ld_acquire(&P.sync->phase);
+    // The acquire that observed the new generation orders these loads after the
+    // decider's writes, so they can all be issued together.
+    S.phase = ld_relaxed(&P.sync->phase);
     S.err = ld_relaxed(&P.sync->err);
     const KState* ks = P.ks;
     S.k = __ldcg(&ks->k);

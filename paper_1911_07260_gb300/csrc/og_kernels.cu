@@ -22,6 +22,8 @@
 // modes share the kernel: the lazy bucket update (Section 3.1: marks during the round,
 // one insertion per marked vertex in the APPLY phase) and unordered Bellman-Ford
 // (QDesc.delta = 0: every improvement goes to bucket cur + 1).
+#include <stddef.h>
+
 #include "og_device.cuh"
 
 namespace og {
@@ -52,11 +54,15 @@ struct Bins {
   uint4* ob;     // outbox: {vertex, distance, query, bucket} of later buckets, this round
 };
 
-// The CTA-local bin a level fills: its entries, their queries and its fill count.
+// The CTA-local bin a level fills: its entries, their queries and its fill count; and
+// the CTA's outbox, where entries bound for the global buckets wait (ob null: such
+// entries go to their buckets at once).
 struct BinOut {
   uint2* e;
   uint16_t* q;
   uint32_t* n;
+  uint4* ob;
+  uint32_t* obn;
 };
 
 struct Cnt {
@@ -95,6 +101,24 @@ __device__ __forceinline__ void insert_warp(const Params& P, Smem& S, const BinO
         C.local++;
       } else {
         dest = 2;  // bin full: the entry goes to the global current bucket
+      }
+    }
+  }
+  if (O.ob) {
+    // Entries for the global buckets wait in the outbox (one shared-memory atomic per
+    // warp), so the warp does not wait for a global append here.
+    const unsigned sm = __ballot_sync(FULL, dest >= 2);
+    if (sm) {
+      const int leader = __ffs(sm) - 1;
+      uint32_t base = 0;
+      if ((int)lane == leader) base = atomicAdd(O.obn, (uint32_t)__popc(sm));
+      base = __shfl_sync(FULL, base, leader);
+      if (dest >= 2) {
+        const uint32_t pos = base + __popc(sm & lanemask_lt());
+        if (pos < kOutbox) {
+          O.ob[pos] = make_uint4(v, nd, q, key);
+          dest = 0;
+        }
       }
     }
   }
@@ -388,21 +412,23 @@ __device__ __forceinline__ void stage_later(const Params& P, Smem& S, const Bins
         }
       }
     }
-    insert_warp(P, S, O, has, false, v, dv, kv, q, C);
+    const BinOut direct = {O.e, O.q, O.n, nullptr, nullptr};
+    insert_warp(P, S, direct, has, false, v, dv, kv, q, C);
   }
 }
 
 // Moves the outbox into the global buckets (ring slot or overflow pile, warp-aggregated).
 // Called by every thread of the CTA; leaves the outbox empty.
-__device__ void flush_outbox(const Params& P, Smem& S, const Bins& B, const BinOut& O, Cnt& C) {
+__device__ void flush_outbox(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   __syncthreads();
   const uint32_t n = min(S.obN, kOutbox);
   const uint32_t lim = (n + 31u) & ~31u;
+  const BinOut direct = {B.e[0], B.q[0], &S.binN[0], nullptr, nullptr};  // never the bin
   for (uint32_t k = threadIdx.x; k < lim; k += kBlock) {
     const bool has = k < n;
     uint4 en = make_uint4(0, 0, 0, 0);
     if (has) en = B.ob[k];
-    insert_warp(P, S, O, has, false, en.x, en.y, en.w, en.z, C);
+    insert_warp(P, S, direct, has, false, en.x, en.y, en.w, en.z, C);
   }
   __syncthreads();
   if (threadIdx.x == 0) S.obN = 0;
@@ -607,13 +633,18 @@ __device__ __forceinline__ void expand_cta(const Params& P, Smem& S, const BinOu
   __syncthreads();  // the lb arrays are refilled by the next call
 }
 
+constexpr uint32_t kQStateWords = sizeof(QState) / 4;
+static_assert(kQStateWords <= 32 && sizeof(QState) % 4 == 0, "QState fits one warp load");
+#define QS_WORD(f) ((uint32_t)(offsetof(QState, f) / 4))
+
 // Run by the CTA that arrives last at a grid barrier, before it releases the others:
 // advances every query's bucket cursor and publishes the next phase and frontier.
 // Every value a decision depends on is read once -- the control words by thread 0 into
 // shared memory, each query's words by lane 0 of its warp and shuffled to the others --
 // so a word that changes while the decider runs (the error word, when a waiting CTA
-// times out) can never send the lanes of a warp down different paths.
-__device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
+// times out) can never send the lanes of a warp down different paths.  A query's state
+// words come in one warp-wide load (every other CTA has arrived: they no longer change).
+__device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Sync* sy = P.sync;
   if (tid == 0) {
@@ -656,9 +687,13 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
   for (uint32_t q = warp; q < P.nq; q += kWarps) {
     QState* qs = P.qs + q;
     uint32_t* cnts = P.counts + (size_t)q * P.B;
-    uint32_t active = warp_ld(&qs->active);
+    // The query's state in one round trip: lane i holds word i of its QState.
+    const uint32_t snap = lane < kQStateWords
+                              ? __ldcg(reinterpret_cast<const uint32_t*>(qs) + lane) : 0u;
+    auto F = [&](uint32_t w) -> uint32_t { return __shfl_sync(FULL, snap, (int)w); };
+    uint32_t active = F(QS_WORD(active));
     uint32_t size = 0;
-    if (active && warp_ld(&qs->aborted)) {
+    if (active && F(QS_WORD(aborted))) {
       active = 0;
       if (lane == 0) {
         qs->active = 0;
@@ -667,8 +702,8 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
       }
     }
     if (active && !fatal) {
-      uint32_t cur = warp_ld(&qs->cur), head = warp_ld(&qs->head), tail = warp_ld(&qs->tail);
-      uint32_t redist = warp_ld(&qs->redist);
+      uint32_t cur = F(QS_WORD(cur)), head = F(QS_WORD(head)), tail = F(QS_WORD(tail));
+      uint32_t redist = F(QS_WORD(redist));
       if (done_phase == kPhRelax) {
         const uint32_t c = cur & P.Bmask;
         const uint32_t cnt = min(warp_ld(cnts + c), P.cap);
@@ -688,7 +723,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
           }
           __syncwarp();
           if (lane == 0) cnts[c] = 0u;
-          const uint32_t ovf_n = warp_ld(&qs->ovf_n), ovf_min = warp_ld(&qs->ovf_min);
+          const uint32_t ovf_n = F(QS_WORD(ovf_n)), ovf_min = F(QS_WORD(ovf_min));
           if (ovf_n > 0 && ovf_min <= next) {
             redist = 1;
             if (lane == 0) {
@@ -705,7 +740,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
           }
         }
       } else if (done_phase == kPhRedistMin && redist) {
-        const uint32_t nc = warp_ld(&qs->redist_min);
+        const uint32_t nc = F(QS_WORD(redist_min));
         if (nc == kInf) {  // every pile entry was out of date and the ring is empty
           active = 0;
           redist = 0;
@@ -714,8 +749,8 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
           cur = nc;
         }
       } else if (done_phase == kPhRedistMove && redist) {
-        const uint32_t sel = warp_ld(&qs->ovf_sel), n2 = warp_ld(&qs->ovf_n2);
-        const uint32_t min2 = warp_ld(&qs->ovf_min2);
+        const uint32_t sel = F(QS_WORD(ovf_sel)), n2 = F(QS_WORD(ovf_n2));
+        const uint32_t min2 = F(QS_WORD(ovf_min2));
         if (lane == 0) {
           qs->ovf_sel = sel ^ 1u;
           qs->ovf_n = n2;
@@ -728,7 +763,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
       const QDesc* qd = P.qd + q;
       const uint32_t kind = __ldg(&qd->kind);
       const uint32_t dst = __ldg(&qd->dst);
-      if (active && !redist && (kind == kPPSP || kind == kASTAR) && !warp_ld(&qs->no_exit)) {
+      if (active && !redist && (kind == kPPSP || kind == kASTAR) && !F(QS_WORD(no_exit))) {
         // Stop rule of Section 6.1 (PPSP): entering bucket i with i * Delta >= the best
         // distance to the target found so far.
         const uint32_t dt = warp_ld(P.dist + (size_t)q * P.n + dst);
@@ -774,6 +809,7 @@ __device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
     if (done_phase == kPhRedistMove) P.stats->v[kStRedist] += 1ull;
   }
 }
+#undef QS_WORD
 
 // Grid-wide barrier with bounded waiting.  The last CTA to arrive runs decide() and then
 // releases the generation word; the others poll it with an acquire load and give up
@@ -810,7 +846,9 @@ __device__ void grid_barrier(const Params& P, Smem& S, uint32_t& bar, uint32_t d
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    S.phase = ld_acquire(&P.sync->phase);
+    // The acquire that observed the new generation orders these after the decider's
+    // writes.
+    S.phase = ld_relaxed(&P.sync->phase);
     S.err = ld_relaxed(&P.sync->err);
     S.t_bar += gtimer() - t_in;
   }
@@ -843,14 +881,19 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
   __syncthreads();
   const uint32_t total = S.pref[P.nq];
   const bool fuse = P.T != 0;
-  const BinOut first = {B.e[0], B.q[0], &S.binN[0]};
+  const BinOut first = {B.e[0], B.q[0], &S.binN[0], B.ob, &S.obN};
   const uint64_t t_start = tid == 0 ? gtimer() : 0ull;
+  // Tiles are claimed one ahead: the claim of the next tile travels while this one is
+  // expanded.
+  uint32_t nxt = 0;
+  if (tid == 0) nxt = atomicAdd(&P.sync->work, P.tile);
   for (;;) {
-    if (tid == 0) S.grab = atomicAdd(&P.sync->work, P.tile);
+    if (tid == 0) S.grab = nxt;
     __syncthreads();
     const uint32_t base = S.grab;
     __syncthreads();
     if (base >= total) break;
+    if (tid == 0) nxt = atomicAdd(&P.sync->work, P.tile);
     for (uint32_t k = tid; k < (ELL ? P.tile : (P.tile + kBlock - 1) / kBlock * kBlock);
          k += kBlock) {
       const uint32_t i = base + k;
@@ -872,17 +915,20 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
       if constexpr (ELL) expand_rows<ASTAR>(P, S, B, first, fuse, has, u, g, q, C);
       else expand_cta(P, S, first, fuse, has, u, g, q, C);
     }
+    __syncthreads();
+    if (S.obN >= kOutbox / 2) flush_outbox(P, S, B, C);  // uniform: read after a barrier
   }
   const uint64_t t_mid = tid == 0 ? gtimer() : 0ull;
   if (tid == 0) S.t_front += t_mid - t_start;
   if (!fuse) {
-    if constexpr (ELL) flush_outbox(P, S, B, first, C);
+    flush_outbox(P, S, B, C);
     return;
   }
   int in = 0;    // entry buffer the level reads
   int cin = 0;   // count word of that buffer
   for (;;) {
     __syncthreads();
+    if (S.obN >= kOutbox / 2) flush_outbox(P, S, B, C);  // uniform: read after a barrier
     const uint32_t nin = S.binN[cin];
     if (nin == 0) break;
     const int cout = cin == 2 ? 0 : cin + 1;
@@ -891,7 +937,7 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
     if (tid == 0) S.binN[cout == 2 ? 0 : cout + 1] = 0;
     const uint32_t cnt = min(nin, P.bin_cap);
     const uint32_t lim = (cnt + 31u) & ~31u;
-    const BinOut O = {B.e[in ^ 1], B.q[in ^ 1], &S.binN[cout]};
+    const BinOut O = {B.e[in ^ 1], B.q[in ^ 1], &S.binN[cout], B.ob, &S.obN};
     if (nin >= P.T) {
       // Large local bucket: hand it to the global bucket for the next round.
       for (uint32_t k = tid; k < lim; k += kBlock) {
@@ -921,7 +967,7 @@ __device__ void relax_phase(const Params& P, Smem& S, const Bins& B, Cnt& C, uin
     cin = cout;
     ++fused;
   }
-  if constexpr (ELL) flush_outbox(P, S, B, first, C);
+  flush_outbox(P, S, B, C);
   __syncthreads();
   if (tid == 0) S.t_fused += gtimer() - t_mid;
 }
@@ -1000,24 +1046,30 @@ __device__ void redist_move_phase(const Params& P) {
 // buckets.
 __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   const uint32_t tid = threadIdx.x, lane = tid & 31;
-  const BinOut O = {B.e[0], B.q[0], &S.binN[0]};  // never written: hub edges go global
+  const BinOut O = {B.e[0], B.q[0], &S.binN[0], nullptr, nullptr};  // hub edges go global
   const uint64_t t_start = tid == 0 ? gtimer() : 0ull;
   for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
   __syncthreads();
   const uint32_t nsub =
       min(warp_ld(reinterpret_cast<const uint32_t*>(&P.sync->big_word)), P.map_cap) * kBigSubs;
+  uint32_t cnext = 0;
+  if (lane == 0) cnext = atomicAdd(&P.sync->big_claim, 1u);
   for (;;) {
-    uint32_t c = 0;
-    if (lane == 0) c = atomicAdd(&P.sync->big_claim, 1u);
-    c = __shfl_sync(FULL, c, 0);
+    const uint32_t c = __shfl_sync(FULL, cnext, 0);
     if (c >= nsub) break;
-    // Lane 0 reads the piece's hub and shuffles it: the loop bounds below enclose
-    // full-warp collectives, so every lane must see the same values.
+    // The next piece is claimed now; its number is only needed after this one, so the
+    // claim's round trip overlaps the work below.
+    if (lane == 0) cnext = atomicAdd(&P.sync->big_claim, 1u);
+    // The piece's hub, read warp-uniformly (the loop bounds below enclose full-warp
+    // collectives): its slot, then the record's six words in one warp-wide load.
     const uint32_t slot = warp_ld(P.big_map + c / kBigSubs);
     if (slot >= P.big_cap) continue;  // chunk of a hub that did not fit (expanded in place)
-    const BigItem* it = P.big + slot;
-    const uint32_t hb = warp_ld(&it->beg), he = warp_ld(&it->end);
-    const uint32_t hg = warp_ld(&it->g), hq = warp_ld(&it->q), cb = warp_ld(&it->cbase);
+    static_assert(sizeof(BigItem) == 6 * sizeof(uint32_t), "BigItem is six words");
+    const uint32_t w = lane < 6 ? __ldcg(reinterpret_cast<const uint32_t*>(P.big + slot) + lane)
+                                : 0u;
+    const uint32_t hg = __shfl_sync(FULL, w, 1), hq = __shfl_sync(FULL, w, 2);
+    const uint32_t hb = __shfl_sync(FULL, w, 3), he = __shfl_sync(FULL, w, 4);
+    const uint32_t cb = __shfl_sync(FULL, w, 5);
     const uint32_t e0 = hb + (c / kBigSubs - cb) * kBigChunk + (c % kBigSubs) * kBigSub;
     for (uint32_t s0 = e0; s0 < min(he, e0 + kBigSub); s0 += 32 * kHeavyBatch) {
       bool ok[kHeavyBatch];
@@ -1041,7 +1093,7 @@ __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
 // updates); its mark is cleared for the next round.
 __device__ void lazy_apply_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   const uint32_t tid = threadIdx.x;
-  const BinOut O = {B.e[0], B.q[0], &S.binN[0]};  // never written: inserts go global
+  const BinOut O = {B.e[0], B.q[0], &S.binN[0], nullptr, nullptr};  // inserts go global
   for (uint32_t q = tid; q < P.nq; q += kBlock) S.cur[q] = __ldcg(&P.qs[q].cur);
   __syncthreads();
   const uint32_t tn = min(warp_ld(&P.sync->lz_n), P.lz_cap);

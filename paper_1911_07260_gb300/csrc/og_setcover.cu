@@ -16,7 +16,10 @@
 // more grid barrier after the pack (A2: classify, claim) and after the count (C: join,
 // cover, move).  One cooperative persistent launch; phases are separated by a bounded
 // grid barrier whose last arriver decides the next phase (sc_decide).
+#include <stddef.h>
+
 #include "og_device.cuh"
+
 #include "og_setcover.cuh"
 
 namespace og {
@@ -489,34 +492,36 @@ __device__ void phase_c(const ScParams& P, const ScSmem& S, ScCnt& C) {
   large_settle(P, S, C);
 }
 
-// Warp-uniform reads for the decider: lane 0 reads, every lane takes its value.  The
-// decider's lane 0 also rewrites some of these words, and the lanes of a warp are not
-// guaranteed to run in lockstep, so a lane reading a word itself could see lane 0's new
-// value while the others saw the old one, decide differently and leave the others
-// waiting in a collective.
-__device__ __forceinline__ uint32_t uread(const uint32_t* p) {
-  uint32_t v = 0;
-  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
-  return __shfl_sync(FULL, v, 0);
-}
-__device__ __forceinline__ unsigned long long uread64(const unsigned long long* p) {
-  unsigned long long v = 0;
-  if ((threadIdx.x & 31) == 0) v = __ldcg(p);
-  return __shfl_sync(FULL, v, 0);
-}
+// The decider's view of ScState: lane i loads word i in one round trip (every other CTA
+// has arrived, so no word changes any more; the error word rides in lane 31), and each
+// field is taken from its lane by a shuffle, so every lane sees the same value (lane 0
+// also rewrites some of these words, and the lanes of a warp are not guaranteed to run in
+// lockstep: a lane reading a word itself could see the new value while the others saw the
+// old one, decide differently and leave the others waiting in a collective).
+constexpr uint32_t kScStateWords = sizeof(ScState) / 4;
+static_assert(kScStateWords <= 31 && sizeof(ScState) % 8 == 0,
+              "ScState and the error word fit one warp load");
+#define SS_WORD(f) ((uint32_t)(offsetof(ScState, f) / 4))
 
 // Run by warp 0 of the CTA that arrives last at a grid barrier: the next phase.  Every
-// value a decision depends on is read warp-uniformly (uread).
+// value a decision depends on is warp-uniform: the state block is read once (snapshot),
+// the band arrays through ballots.
 __device__ void sc_decide(const ScParams& P, uint32_t done) {
   const uint32_t lane = threadIdx.x & 31;
   ScState* ss = P.ss;
-  const bool fatal = (uread(&P.sync->err) & kErrFatal) != 0u;
+  const uint32_t snap = lane < kScStateWords
+                            ? __ldcg(reinterpret_cast<const uint32_t*>(ss) + lane)
+                            : (lane == 31 ? ld_relaxed(&P.sync->err) : 0u);
+  auto F = [&](uint32_t w) -> uint32_t { return __shfl_sync(FULL, snap, (int)w); };
+  const bool fatal = (F(31) & kErrFatal) != 0u;
   uint32_t next = kScStop;
-  auto large_n = [&](uint32_t sel) -> uint32_t {
-    return (uint32_t)(uread64(&ss->bw[sel]) >> kScCntShift);
+  auto large_n = [&](uint32_t sel) -> uint32_t {  // entries of large member list sel
+    const uint32_t lo = F(SS_WORD(bw) + 2 * sel), hi = F(SS_WORD(bw) + 2 * sel + 1);
+    return (uint32_t)((((unsigned long long)hi << 32) | lo) >> kScCntShift);
   };
   // The highest non-empty band at or below `from`; its largest bucket is gathered next.
   auto transition = [&](int from) -> uint32_t {
+    const uint32_t gathers = F(SS_WORD(gathers));
     for (int top = from; top >= 0; top -= 32) {
       const int b = top - (int)lane;
       const bool ne = b >= 0 && __ldcg(P.bcnt + b) > 0u;
@@ -530,7 +535,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
           ss->gcnt = 0u;
           ss->ns[0] = ss->ns[1] = 0u;
           ss->bw[0] = ss->bw[1] = 0ull;
-          ss->gathers = __ldcg(&ss->gathers) + 1u;
+          ss->gathers = gathers + 1u;
         }
         return kScGather;
       }
@@ -540,9 +545,10 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
   // A step either adds a set to the cover or empties its bucket (every member leaves or
   // moves down), so a run takes at most n + nb steps; more means a broken invariant.
   auto start_step = [&]() -> uint32_t {
-    const uint32_t s = uread(&ss->step) + 1u;
+    const uint32_t s = F(SS_WORD(step)) + 1u;
+    const uint32_t j = F(SS_WORD(j));
     if ((unsigned long long)s > (unsigned long long)P.n + P.nb + 1ull) {
-      if (lane == 0) report_bad(P.sync, 63u, s, __ldcg(&ss->j));
+      if (lane == 0) report_bad(P.sync, 63u, s, j);
       return kScStop;
     }
     if (lane == 0) {
@@ -552,20 +558,22 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
     return kScA;
   };
   if (!fatal) {
-    const uint32_t c = uread(&ss->csel) & 1u;
+    const uint32_t c = F(SS_WORD(csel)) & 1u;
     switch (done) {
       case kScPrologue:
         next = transition((int)P.nbands - 1);
         break;
       case kScGather: {
-        const uint32_t b = uread(&ss->band);
+        const uint32_t b = F(SS_WORD(band));
+        const uint32_t gcnt = F(SS_WORD(gcnt)), gmax = F(SS_WORD(gmax));
         if (lane == 0) {
           P.bsel[b] = __ldcg(P.bsel + b) ^ 1u;
-          P.bcnt[b] = __ldcg(&ss->gcnt);
-          P.bmax[b] = __ldcg(&ss->gmax);
+          P.bcnt[b] = gcnt;
+          P.bmax[b] = gmax;
         }
-        if (uread(&ss->ns[c]) + large_n(c) == 0u) {
-          if (lane == 0) report_bad(P.sync, 54u, __ldcg(&ss->j), b);
+        if (F(SS_WORD(ns) + c) + large_n(c) == 0u) {
+          const uint32_t j = F(SS_WORD(j));
+          if (lane == 0) report_bad(P.sync, 54u, j, b);
           next = kScStop;
         } else {
           next = start_step();
@@ -585,7 +593,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
           break;
         }
         const uint32_t x = c ^ 1u;
-        if (uread(&ss->ns[x]) + large_n(x) > 0u) {
+        if (F(SS_WORD(ns) + x) + large_n(x) > 0u) {
           if (lane == 0) {
             ss->csel = x;
             ss->ns[c] = 0u;
@@ -593,7 +601,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
           }
           next = start_step();
         } else {
-          next = transition((int)uread(&ss->band));
+          next = transition((int)F(SS_WORD(band)));
         }
         break;
       }
@@ -604,6 +612,7 @@ __device__ void sc_decide(const ScParams& P, uint32_t done) {
   __syncwarp();
   if (lane == 0) P.sync->phase = next;
 }
+#undef SS_WORD
 
 // Bounded grid barrier: the last CTA to arrive runs sc_decide and releases the others,
 // who give up after spin_ns or on a fatal error.
@@ -639,7 +648,9 @@ __device__ void sc_barrier(const ScParams& P, ScSmem& S, uint32_t& bar, uint32_t
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    S.phase = ld_acquire(&P.sync->phase);
+    // The acquire that observed the new generation orders these loads after the
+    // decider's writes, so they can be issued together.
+    S.phase = ld_relaxed(&P.sync->phase);
     S.err = ld_relaxed(&P.sync->err);
     const ScState* ss = P.ss;
     S.j = __ldcg(&ss->j);
