@@ -81,6 +81,9 @@ def parse_args(argv=None):
     p.add_argument("--serve-fusion", type=int, default=64, help="serve: fusion threshold")
     p.add_argument("--sequential", type=int, default=2000,
                    help="serve: queries in the one-at-a-time baseline")
+    p.add_argument("--pull-divisor", type=int, default=0,
+                   help="direction optimisation: pull a query's round when its frontier "
+                        "exceeds n / this (0 = always push)")
     p.add_argument("--no-batch", action="store_true",
                    help="default workload: skip the 256-query batch measurement")
     p.add_argument("--launch-check", action="store_true",
@@ -289,6 +292,9 @@ def run_ours(args):
     if args.arena:
         cfg = cfg if cfg is not None else og.config()
         cfg.arena_entries = args.arena
+    if args.pull_divisor:
+        cfg = cfg if cfg is not None else og.config()
+        cfg.pull_divisor = args.pull_divisor
     eff = G.get_config() if cfg is None else cfg
     queries = [(kind, int(s), 0, 0) for s in srcs]
     nq = len(queries)
@@ -431,6 +437,7 @@ def run_ours(args):
                        "blocks_per_sm": int(eff.blocks_per_sm),
                        "engine": "async" if int(eff.engine) == 2 else "rounds",
                        "layout": "ell" if int(eff.layout) == 2 else "csr",
+                       "pull_divisor": int(eff.pull_divisor),
                        "prefetch": int(eff.prefetch) == 1,
                        "bucket_update": "lazy" if int(eff.bucket_update) == 2 else "eager",
                        "l2": "inputs larger than L2 (graph %.0f MB + dist %.0f MB > 129 MB)"

@@ -100,7 +100,14 @@ typedef struct og_config {
                                 marked vertex makes one insertion, into the bucket of
                                 its final distance (the buffer reduction).  Lazy turns
                                 fusion off and runs on the round engine.                */
-  uint32_t reserved2;
+  uint32_t pull_divisor;     /* direction optimisation (the pull direction of Section 4.2's
+                                scheduling language; round engine, SSSP / wBFS queries):
+                                a query's round pulls -- every vertex not yet settled
+                                scans its in-edges for neighbours in the current bucket
+                                -- when its frontier holds more than n / pull_divisor
+                                entries, and pushes otherwise.  0 = always push (the
+                                default).  The in-edges are built on the device the first
+                                time a pull is asked for and kept with the graph.      */
   uint64_t spin_limit_ns;    /* cap on each grid-barrier wait (default 2 s)            */
   uint64_t arena_entries;    /* bucket-entry capacity per query (ring + overflow)      */
 } og_config;

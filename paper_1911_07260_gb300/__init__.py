@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
                 ("ring_buckets", ctypes.c_uint32), ("engine", ctypes.c_uint32),
                 ("precheck", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("prefetch", ctypes.c_uint32), ("hub_degree", ctypes.c_uint32),
-                ("bucket_update", ctypes.c_uint32), ("reserved2", ctypes.c_uint32),
+                ("bucket_update", ctypes.c_uint32), ("pull_divisor", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("arena_entries", ctypes.c_uint64)]
 
     def as_dict(self):

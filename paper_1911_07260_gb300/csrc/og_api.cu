@@ -34,6 +34,10 @@ cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj
                               uint32_t n, uint32_t* flags, int sms, cudaStream_t st);
 cudaError_t launch_check_csr(const uint32_t* off, const uint2* adj, uint32_t n, uint32_t m,
                              uint32_t* flags, int sms, cudaStream_t st);
+cudaError_t launch_indeg(const uint32_t* off, const uint2* adj, uint32_t n, uint32_t* deg, int sms,
+                         cudaStream_t st);
+cudaError_t launch_transpose(const uint32_t* off, const uint2* adj, uint32_t n, const uint32_t* toff,
+                             uint32_t* cursor, uint2* tadj, int sms, cudaStream_t st);
 cudaError_t launch_async(const AParams& P, int grid, size_t smem, cudaStream_t st);
 cudaError_t async_occupancy(int* blocks_per_sm, size_t smem, bool ell);
 cudaError_t launch_async_init(const AParams& P, const uint32_t* slots, uint32_t nslots,
@@ -222,6 +226,8 @@ struct og_graph {
   uint32_t* off = nullptr;
   uint2* adj = nullptr;
   uint4* ell = nullptr;      // ELL-8 rows when every degree is <= 8
+  uint32_t* toff = nullptr;  // transpose (in-edges), built the first time a pull is asked for
+  uint2* tadj = nullptr;
   uint32_t max_deg = 0;
   float2* xy = nullptr;
   std::vector<float> h_xy;   // host copy: target coordinates of A* queries
@@ -284,6 +290,7 @@ og_config resolve(const og_graph* g, const og_config* user) {
   r.spin_limit_ns = pick64(u.spin_limit_ns, g->cfg.spin_limit_ns, kDefaultSpinNs);
   r.arena_entries = pick64(u.arena_entries, g->cfg.arena_entries, 0);
   r.engine = u.engine ? u.engine : g->cfg.engine;
+  r.pull_divisor = u.pull_divisor ? u.pull_divisor : g->cfg.pull_divisor;
   r.precheck = u.precheck ? u.precheck : g->cfg.precheck;
   r.layout = u.layout ? u.layout : g->cfg.layout;
   // layout 0 stays "automatic": the round engine picks its ELL row path (two dependent
@@ -343,6 +350,56 @@ struct RunOut {
   uint32_t err = 0;
   uint64_t restarts = 0;
 };
+
+// The in-edge lists of the graph (for pull rounds), built on the device the first time a
+// pull is asked for and kept with the graph: in-degrees, their prefix sums (on the
+// host), then a scatter of every edge.
+int ensure_transpose(og_graph* g, cudaStream_t st) {
+  if (g->toff) return OG_OK;
+  const uint32_t n = g->n;
+  uint32_t* toff = nullptr;
+  uint32_t* cur = nullptr;
+  uint2* tadj = nullptr;
+  std::vector<uint32_t> h(n + 1, 0u);
+  int dev = 0;
+  auto fail = [&](cudaError_t e, const char* what) {
+    if (toff) cudaFree(toff);
+    if (cur) cudaFree(cur);
+    if (tadj) cudaFree(tadj);
+    return cuda_fail(e, what);
+  };
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && !g->sms)
+    e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(e, "device query");
+  if ((e = cudaMalloc(&toff, sizeof(uint32_t) * ((size_t)n + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&cur, sizeof(uint32_t) * (size_t)n)) != cudaSuccess ||
+      (e = cudaMalloc(&tadj, sizeof(uint2) * std::max<uint64_t>(1, g->m))) != cudaSuccess)
+    return fail(e, "transpose allocation");
+  if ((e = cudaMemsetAsync(cur, 0, sizeof(uint32_t) * (size_t)n, st)) != cudaSuccess ||
+      (e = launch_indeg(g->off, g->adj, n, cur, g->sms, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h.data(), cur, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost,
+                           st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(e, "in-degrees");
+  uint32_t run = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    const uint32_t x = h[v];
+    h[v] = run;
+    run += x;
+  }
+  h[n] = run;
+  if ((e = cudaMemcpyAsync(toff, h.data(), sizeof(uint32_t) * ((size_t)n + 1),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(cur, 0, sizeof(uint32_t) * (size_t)n, st)) != cudaSuccess ||
+      (e = launch_transpose(g->off, g->adj, n, toff, cur, tadj, g->sms, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(e, "transpose");
+  cudaFree(cur);
+  g->toff = toff;
+  g->tadj = tadj;
+  return OG_OK;
+}
 
 // Round-synchronous engine: up to kMaxQ queries in one persistent launch, regrowing the
 // arena when a query runs out of bucket space.  dist_dev: nq*n device words (query i at
@@ -430,6 +487,12 @@ int run_chunk_rounds(og_graph* g, Workspace& ws, const QDesc* qd, uint32_t nq, c
     P.precheck = c.precheck == OG_PRECHECK_ON ? 1u : 0u;
     P.prefetch = c.prefetch == OG_PREFETCH_OFF ? 0u : 1u;
     P.spin_ns = c.spin_limit_ns;
+    if (c.pull_divisor && c.bucket_update != OG_UPDATE_LAZY) {
+      TRY(ensure_transpose(g, st));
+      P.pull_div = c.pull_divisor;
+      P.toff = g->toff;
+      P.tadj = g->tadj;
+    }
     if (c.bucket_update == OG_UPDATE_LAZY) {  // marks instead of inserts; no fusion
       const uint32_t words = (g->n + 31) / 32;
       // One mark per (vertex, query) and round; at most 2^28 marks a round (2 GB).
@@ -938,6 +1001,8 @@ void og_graph_free(og_graph* g) {
   if (g->adj) cudaFree(g->adj);
   if (g->ell) cudaFree(g->ell);
   if (g->xy) cudaFree(g->xy);
+  if (g->toff) cudaFree(g->toff);
+  if (g->tadj) cudaFree(g->tadj);
   delete g;
 }
 

@@ -47,6 +47,8 @@ enum Phase : uint32_t {
   kPhPrologue = 4,   // kernel start: publish the frontier of the current state
   kPhBig = 5,        // edges of very-high-degree vertices, split over all CTAs
   kPhApply = 6,      // lazy bucket update: one insertion per vertex marked this round
+  kPhPull = 7,       // direction optimisation: queries with a large frontier pull (every
+                     // unsettled vertex scans its in-edges for current-bucket neighbours)
 };
 
 // A vertex whose out-degree is at least Params::hub_min (a hub of a skewed graph) is not
@@ -83,7 +85,8 @@ struct QState {
   uint32_t no_exit;      // A*: early exit disabled (a key fell below the cursor)
   uint32_t result;       // dist(src, dst) once finished
   uint32_t aborted;      // bucket arena exhausted: the query stopped early
-  uint32_t pad[2];
+  uint32_t pull;         // this round's frontier is processed by a pull phase
+  uint32_t pad;
 };
 
 struct Sync {
@@ -153,6 +156,11 @@ struct Params {
   uint2* lz_list;         // {vertex, query} marked this round
   uint32_t lz_cap;
   unsigned long long spin_ns;
+  // Direction optimisation (pull_div 0 = off): a query's round is a pull phase when its
+  // frontier holds more than n / pull_div entries; tin / tadj = the in-edges (transpose).
+  uint32_t pull_div;
+  const uint32_t* toff;
+  const uint2* tadj;      // {source, weight} per in-edge
 };
 
 // ---- barrier-free engine (og_async.cu) -----------------------------------------------

@@ -40,7 +40,7 @@ struct Smem {
   uint32_t last;
   uint32_t phase;
   uint32_t err;
-  uint32_t f_active, f_redist;
+  uint32_t f_active, f_redist, f_pull;
   uint32_t d_err, d_big, d_lz;  // decider: control words read once by thread 0
   uint32_t wtmp[kWarps + 1];
   uint32_t lb_pos[kBlock + 1];  // CTA-wide expansion: edge prefix sums of the entries
@@ -644,7 +644,7 @@ static_assert(kQStateWords <= 32 && sizeof(QState) % 4 == 0, "QState fits one wa
 // so a word that changes while the decider runs (the error word, when a waiting CTA
 // times out) can never send the lanes of a warp down different paths.  A query's state
 // words come in one warp-wide load (every other CTA has arrived: they no longer change).
-__device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
+__device__ void decide(const Params& P, Smem& S, uint32_t done_phase) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Sync* sy = P.sync;
   if (tid == 0) {
@@ -653,6 +653,7 @@ __device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phas
     S.d_lz = ld_relaxed(&sy->lz_n);
     S.f_active = 0;
     S.f_redist = 0;
+    S.f_pull = 0;
   }
   __syncthreads();
   const uint32_t err = S.d_err;
@@ -704,7 +705,9 @@ __device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phas
     if (active && !fatal) {
       uint32_t cur = F(QS_WORD(cur)), head = F(QS_WORD(head)), tail = F(QS_WORD(tail));
       uint32_t redist = F(QS_WORD(redist));
-      if (done_phase == kPhRelax) {
+      // A pull phase consumed the frontier of the queries it pulled: for them it ends the
+      // round like a relax phase; the others keep their frontier for the relax phase.
+      if (done_phase == kPhRelax || (done_phase == kPhPull && F(QS_WORD(pull)))) {
         const uint32_t c = cur & P.Bmask;
         const uint32_t cnt = min(warp_ld(cnts + c), P.cap);
         if (cnt > tail) {  // the current bucket received entries: process it again
@@ -770,17 +773,23 @@ __device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phas
         if (dt != kInf && (unsigned long long)cur * __ldg(&qd->delta) >= dt) active = 0;
       }
       const uint32_t res = (!active && dst < P.n) ? warp_ld(P.dist + (size_t)q * P.n + dst) : 0u;
+      // Direction optimisation: an SSSP / wBFS query whose frontier exceeds n / pull_div
+      // pulls this round instead of pushing.
+      const bool pull = P.pull_div && active && !redist && kind == kSSSP &&
+                        __ldg(&qd->delta) != 0u && tail - head > P.n / P.pull_div;
       if (lane == 0) {
         qs->cur = cur;
         qs->head = head;
         qs->tail = tail;
         qs->redist = redist;
         qs->active = active;
+        qs->pull = pull ? 1u : 0u;
         if (!active) qs->result = res;
         if (active) S.f_active = 1;
         if (redist) S.f_redist = 1;
+        if (pull) S.f_pull = 1;
       }
-      size = (active && !redist) ? tail - head : 0u;
+      size = (active && !redist && !pull) ? tail - head : 0u;
     }
     if (lane == 0) S.pref[q] = size;
   }
@@ -797,7 +806,8 @@ __device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phas
       else
         next = S.f_redist ? kPhRedistMin : (S.f_active ? kPhRelax : kPhStop);
     }
-    if (next == kPhRelax) {
+    if (next == kPhRelax && S.f_pull) next = kPhPull;  // pulls first, then the pushes
+    if (next == kPhRelax || next == kPhPull) {
       if (sy->rounds >= P.max_rounds) next = kPhStop;
       else sy->rounds = sy->rounds + 1;
     }
@@ -805,7 +815,7 @@ __device__ __noinline__ void decide(const Params& P, Smem& S, uint32_t done_phas
     sy->work = 0;
     sy->total = S.pref[P.nq];
     sy->any_active = S.f_active;
-    P.stats->v[kStRounds] += (next == kPhRelax) ? 1ull : 0ull;
+    P.stats->v[kStRounds] += (next == kPhRelax || next == kPhPull) ? 1ull : 0ull;
     if (done_phase == kPhRedistMove) P.stats->v[kStRedist] += 1ull;
   }
 }
@@ -1088,6 +1098,98 @@ __device__ void big_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
   if (tid == 0) S.t_hub += gtimer() - t_start;
 }
 
+// Direction optimisation (the pull direction of Section 4.2's scheduling language): for
+// a query whose frontier is large, every vertex not yet settled (its bucket >= the
+// current one) scans its in-edges and takes the best distance through a neighbour of
+// the current bucket, instead of the frontier pushing along its out-edges.  Each vertex
+// is written only by the warp that owns it (no atomics on the destination); an
+// improvement is inserted like a pushed one.  The in-edges of a warp's 32 vertices are
+// walked together (flattened as in expand_warp), and each edge lowers its owner's best
+// candidate with a shared-memory atomicMin.  Every current-bucket vertex acts as a source,
+// a superset of the round's frontier, so the result is the push round's or better.
+__device__ void pull_phase(const Params& P, Smem& S, const Bins& B, Cnt& C) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (uint32_t q = tid; q < P.nq; q += kBlock) {
+    S.cur[q] = __ldcg(&P.qs[q].cur);
+    S.head[q] = __ldcg(&P.qs[q].pull);  // scratch: the query pulls this phase
+  }
+  if (tid == 0) S.obN = 0;
+  __syncthreads();
+  const BinOut O = {B.e[0], B.q[0], &S.binN[0], B.ob, &S.obN};  // never the bin
+  uint32_t* wbest = S.lb_pos + warp * 32;  // best candidate of each lane's vertex
+  const uint32_t gwarp = blockIdx.x * kWarps + warp, nwarp = gridDim.x * kWarps;
+  for (uint32_t q = 0; q < P.nq; ++q) {
+    if (!S.head[q]) continue;  // uniform: shared memory
+    const uint32_t cur = S.cur[q], dl = S.delta[q];
+    uint32_t* dq = P.dist + (size_t)q * P.n;
+    for (uint32_t v0 = gwarp * 32; v0 < P.n; v0 += nwarp * 32) {
+      const uint32_t v = v0 + lane;
+      bool has = v < P.n;
+      const uint32_t d = has ? __ldcg(dq + v) : 0u;
+      if (has && d != kInf && d / dl < cur) has = false;  // settled in an earlier bucket
+      uint32_t beg = 0, end = 0;
+      if (has) {
+        beg = __ldg(P.toff + v);
+        end = __ldg(P.toff + v + 1);
+      }
+      wbest[lane] = has ? d : kInf;
+      __syncwarp();
+      const uint32_t deg = end - beg;
+      uint32_t incl = deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if ((int)lane >= o) incl += t;
+      }
+      const uint32_t total = __shfl_sync(FULL, incl, 31);
+      const uint32_t excl = incl - deg;
+      for (uint32_t base = 0; base < total; base += 32 * kLightBatch) {
+        bool ok[kLightBatch];
+        uint32_t own[kLightBatch];
+        uint2 iw[kLightBatch];
+#pragma unroll
+        for (int k = 0; k < kLightBatch; ++k) {
+          const uint32_t idx = base + 32u * k + lane;
+          uint32_t pos = 0;  // owner lane: number of lanes whose inclusive sum is <= idx
+#pragma unroll
+          for (int s = 16; s > 0; s >>= 1) {
+            const uint32_t x = __shfl_sync(FULL, incl, pos + s - 1);
+            if (x <= idx) pos += s;
+          }
+          const uint32_t ob = __shfl_sync(FULL, beg, pos), oe = __shfl_sync(FULL, excl, pos);
+          ok[k] = idx < total;
+          own[k] = pos;
+          iw[k] = ok[k] ? __ldg(P.tadj + ob + (idx - oe)) : make_uint2(0u, 0u);
+        }
+        uint32_t du[kLightBatch];
+#pragma unroll
+        for (int k = 0; k < kLightBatch; ++k) du[k] = ok[k] ? __ldcg(dq + iw[k].x) : kInf;
+#pragma unroll
+        for (int k = 0; k < kLightBatch; ++k) {
+          if (ok[k]) {
+            C.relax++;
+            if (du[k] != kInf && du[k] / dl == cur) {
+              const unsigned long long sum = (unsigned long long)du[k] + iw[k].y;
+              atomicMin(wbest + own[k], sum >= kSat ? kSat : (uint32_t)sum);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      const uint32_t best = wbest[lane];
+      const bool ins = has && best < d;
+      if (ins) {
+        if (best >= kSat) atomicOr(&P.sync->err, kErrSat);
+        dq[v] = best;
+        C.improved++;
+      }
+      __syncwarp();
+      insert_warp(P, S, O, ins, false, v, best, ins ? best / dl : 0u, q, C);
+    }
+  }
+  flush_outbox(P, S, B, C);
+}
+
 // The lazy bucket update's reduction (Section 3.1): every vertex marked this round is
 // inserted once, into the bucket of its distance now (the minimum of the round's
 // updates); its mark is cleared for the next round.
@@ -1146,6 +1248,7 @@ __device__ __forceinline__ void delta_body(const Params& P) {
     else if (phase == kPhRedistMin) redist_min_phase(P);
     else if (phase == kPhRedistMove) redist_move_phase(P);
     else if (phase == kPhApply) lazy_apply_phase(P, S, B, C);
+    else if (phase == kPhPull) pull_phase(P, S, B, C);
     else if (phase == kPhBig) {
       if constexpr (!ELL) big_phase(P, S, B, C);  // ELL rows hold <= 8 edges: no hubs
     }
@@ -1228,7 +1331,8 @@ extern "C" __global__ void og_init_kernel(Params P, const uint32_t* slots, uint3
   s.no_exit = 0;
   s.result = kInf;
   s.aborted = 0;
-  s.pad[0] = s.pad[1] = 0;
+  s.pull = 0;
+  s.pad = 0;
   P.qs[q] = s;
 }
 
@@ -1336,6 +1440,42 @@ cudaError_t launch_init(const Params& P, const uint32_t* slots, uint32_t nslots,
 cudaError_t launch_interleave(const uint32_t* nbr, const uint32_t* w, uint2* adj, size_t m,
                               uint32_t n, uint32_t* flags, int sms, cudaStream_t st) {
   og_interleave_kernel<<<sms * 4, 256, 0, st>>>(nbr, w, adj, m, n, flags);
+  return cudaGetLastError();
+}
+
+// The transpose (in-edges) for the pull direction: in-degrees counted with atomicAdd,
+// then every edge u -> v scattered to v's in-edge list as {u, weight} (the order within a
+// list does not matter: a pull takes the minimum over it).  One warp per source vertex.
+extern "C" __global__ void og_indeg_kernel(const uint32_t* off, const uint2* adj, uint32_t n,
+                                           uint32_t* deg) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t u = w0; u < n; u += nw)
+    for (uint32_t e = off[u] + lane; e < off[u + 1]; e += 32) atomicAdd(deg + adj[e].x, 1u);
+}
+extern "C" __global__ void og_transpose_kernel(const uint32_t* off, const uint2* adj, uint32_t n,
+                                               const uint32_t* toff, uint32_t* cursor,
+                                               uint2* tadj) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t u = w0; u < n; u += nw)
+    for (uint32_t e = off[u] + lane; e < off[u + 1]; e += 32) {
+      const uint2 a = adj[e];
+      const uint32_t pos = atomicAdd(cursor + a.x, 1u);
+      tadj[toff[a.x] + pos] = make_uint2(u, a.y);
+    }
+}
+
+cudaError_t launch_indeg(const uint32_t* off, const uint2* adj, uint32_t n, uint32_t* deg, int sms,
+                         cudaStream_t st) {
+  og_indeg_kernel<<<sms * 8, 256, 0, st>>>(off, adj, n, deg);
+  return cudaGetLastError();
+}
+cudaError_t launch_transpose(const uint32_t* off, const uint2* adj, uint32_t n, const uint32_t* toff,
+                             uint32_t* cursor, uint2* tadj, int sms, cudaStream_t st) {
+  og_transpose_kernel<<<sms * 8, 256, 0, st>>>(off, adj, n, toff, cursor, tadj);
   return cudaGetLastError();
 }
 

@@ -673,3 +673,57 @@ def test_server_slot_reuse_resets_the_reached_blocks(og, orc, gg, road300):
     for j, (s, t) in enumerate(pairs.tolist()):
         if kinds[j] != og.Q_SSSP:
             assert got[j] == orc.ppsp(g, s, t), (j, kinds[j])
+
+
+ALWAYS_PULL = 0xFFFFFFFF  # pull whenever a query's frontier is non-empty
+
+
+@pytest.mark.parametrize("delta", [1, 16, 1000])
+def test_pull_rounds_match_oracle_on_skewed_and_road_graphs(og, orc, gg, delta):
+    """Direction optimisation: rounds in which every unsettled vertex pulls from its
+    in-neighbours of the current bucket give the oracle's distances -- forced on every
+    round, and only on large frontiers -- for SSSP on R-MAT (weights up to 1000) and a
+    road-like grid, and for wBFS."""
+    for g in (gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1000, seed=7), gg.road(120, seed=7)):
+        G = og.Graph.from_csr(g)
+        src = int(gg.sample_sources(g, 1, seed=5)[0])
+        ref = orc.dijkstra(g, src)
+        for div in (ALWAYS_PULL, 8):
+            for fusion in (0xFFFFFFFE, 256):
+                cfg = og.config(delta=delta, pull_divisor=div, fusion_threshold=fusion,
+                                layout=og.LAYOUT_CSR)
+                got, _, st = og.query_run(G, og.Q_SSSP, src, cfg=cfg)
+                np.testing.assert_array_equal(got, ref, err_msg=f"{g.name} {div} {fusion}")
+        w1 = gg.with_weights(g, 1, 24, seed=3)
+        G1 = og.Graph.from_csr(w1)
+        got, _, _ = og.query_run(G1, og.Q_WBFS, src, cfg=og.config(pull_divisor=ALWAYS_PULL))
+        np.testing.assert_array_equal(got, orc.dijkstra(w1, src))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_pull_rounds_on_directed_multigraphs(og, orc, gg, seed):
+    """Pull reads the in-edges (the transpose the library builds): directed graphs with
+    parallel edges, self loops and zero weights, pulled on every round."""
+    g = gg.random_graph(int(1500 + 300 * seed), 9000 + 1000 * seed, wlo=0, whi=60,
+                        seed=40 + seed, symmetric=False)
+    G = og.Graph.from_csr(g)
+    src = int(gg.sample_sources(g, 1, seed=seed)[0])
+    got, _, _ = og.query_run(G, og.Q_SSSP, src, cfg=og.config(delta=8, pull_divisor=ALWAYS_PULL))
+    np.testing.assert_array_equal(got, orc.dijkstra(g, src))
+
+
+def test_pull_rounds_in_a_mixed_batch(og, orc, gg, road300):
+    """SSSP queries pull while PPSP, A* and Bellman-Ford queries of the same launch push."""
+    g, G = road300
+    srcs = gg.sample_sources(g, 4, seed=77)
+    pairs = gg.sample_pairs_grid_steps(g, 4, 5, 150, seed=78)
+    qs = [(og.Q_SSSP, int(s), 0, 0) for s in srcs[:3]] + [(og.Q_BF, int(srcs[3]), 0, 0)] + \
+         [(og.Q_PPSP if i % 2 else og.Q_ASTAR, int(a), int(b), 0) for i, (a, b) in enumerate(pairs)]
+    out, d, _ = og.batch_run(G, qs, cfg=og.config(delta=512, pull_divisor=16,
+                                                  fusion_threshold=128))
+    rows = out.reshape(len(qs), g.n)
+    for i, (kind, s, t, _) in enumerate(qs):
+        if kind in (og.Q_SSSP, og.Q_BF):
+            np.testing.assert_array_equal(rows[i], orc.dijkstra(g, s))
+        else:
+            assert int(d[i]) == orc.ppsp(g, s, t)
