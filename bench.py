@@ -188,11 +188,12 @@ def clock_summary(lines) -> dict:
             "power_w_max": max(float(r[3] or 0) for r in rows)}
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of og_delta_kernel from one
-# ncu capture on the road-like 2400 x 2400 graph with 8 sources (the full 4900 x 4900 launch
-# is too large for a multi-pass capture), scaled by vertices x sources to the benchmarked
-# graph.  It describes the kernel sources it was taken on; any other build reports null.
-TRAFFIC_CAPTURE = {"kernel_sha": "395f6120cfae60ea", "bytes": 1.2007e9, "n": 5756935,
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of og_delta_ell_kernel from
+# one ncu capture on the road-like 2400 x 2400 graph with 8 sources (the full 4900 x 4900
+# launch is too large for a multi-pass capture), scaled by vertices x sources to the
+# benchmarked graph.  It describes the kernel sources it was taken on; any other build
+# reports null.
+TRAFFIC_CAPTURE = {"kernel_sha": "e39c40888107d6d6", "bytes": 2.5669e9, "n": 5756935,
                    "sources": 8, "kind": "road"}
 KERNEL_SOURCES = ["paper_1911_07260_gb300/csrc/og_kernels.cu",
                   "paper_1911_07260_gb300/csrc/og_device.cuh",
@@ -348,11 +349,16 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / kernel_s / 1e9
+    # The persistent kernel that ran: ELL rows where every degree is <= 8 (layout 0 =
+    # automatic, 2 = ELL) for the eager update, the CSR kernel otherwise.
+    ell_rows = int(np.diff(g.offsets).max(initial=0)) <= 8 and int(eff.layout) in (0, 2) \
+        and int(eff.bucket_update) != 2
+    kname = "og_delta_ell_kernel" if ell_rows else "og_delta_kernel"
     traffic = scaled_traffic({"road-sssp": "road", "road-bf": "bf"}.get(args.workload, "rmat"),
-                             g.n, nq, int(eff.engine))
+                             g.n, nq, int(eff.engine)) if ell_rows else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_kind, "kernel": "og_delta_kernel",
+                "peak_source": peak_kind, "kernel": kname,
                 "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": round(kernel_s * 1e3, 3)}
 
