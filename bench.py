@@ -362,6 +362,25 @@ def run_ours(args):
                 "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": round(kernel_s * 1e3, 3)}
 
+    if not ell_rows:
+        # The CSR path's relaxations are independent random 4-byte accesses (the stale
+        # check and the offsets of each expanded vertex, the pre-check load of each edge,
+        # the atomicMin of each improvement); their ceiling is the rate at which the
+        # memory system serves such accesses, measured here by the probe: uniform random
+        # loads over a 512 MiB array (the distances of 8 queries on R-MAT scale 24) at
+        # the persistent kernel's occupancy, 4 independent loads per thread.
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        ctas, threads, w = 3 * sms, 256, 4
+        ra_peak = ctas * threads * w / og.probe_chain(2, 512 << 20, ctas, threads, 100, 0, w)
+        per = {k: v / args.steps for k, v in agg.items()}
+        acc = 2 * per["items"] + per["relax"] + per["improved"]
+        ra = acc / kernel_s / 1e9
+        roofline["random_access"] = {
+            "achieved": round(ra, 1), "peak": round(ra_peak, 1), "unit": "G accesses/s",
+            "frac": round(ra / ra_peak, 3), "accesses_per_launch": int(acc),
+            "peak_source": "measured in this run: og_probe_chain, uniform random 4-byte "
+                           "loads over 512 MiB, %d x %d threads x %d" % (ctas, threads, w)}
+
     eager = None
     if eager_ref is not None:
         og.batch_run(G, queries, cfg=eager_ref, out=dbuf)
@@ -1055,6 +1074,21 @@ def probe_latency(og, ctas: int, threads: int) -> dict:
     return out
 
 
+def probe_throughput(og, ctas: int, threads: int) -> dict:
+    """Independent random accesses a second (G/s) with 1-16 chains per thread at the
+    persistent kernels' occupancy: 4-byte loads through L1 (the pre-check's loads) and
+    atomicMins, over a 512 MiB array (the distances of 8 queries on R-MAT scale 24) and
+    a 4 GiB one.  The rate the memory system serves random accesses at is the ceiling
+    of a relaxation pass whose accesses are independent."""
+    out = {}
+    for size_name, nbytes in (("512MiB", 512 << 20), ("4GiB", 4 << 30)):
+        for mode_name, mode in (("load", 2), ("atomic", 1)):
+            for w in (1, 2, 4, 8, 16):
+                ns = og.probe_chain(mode, nbytes, ctas, threads, 100, 0, w)
+                out[f"{mode_name}_{size_name}_x{w}"] = round(ctas * threads * w / ns, 1)
+    return out
+
+
 def run_latency(args):
     """The memory round-trip probe alone (ns per dependent access; lower is better)."""
     import torch
@@ -1064,6 +1098,7 @@ def run_latency(args):
     ctas, threads = sms * 3, 256
     with ClockSampler(0) as clk:
         lat = probe_latency(og, ctas, threads)
+        thr = probe_throughput(og, ctas, threads)
     clocks = clk.summary()
     line = {"metric": "memory round trip, ns per dependent access", "value":
             lat["atomic_l2_8MiB_loaded"], "unit": "ns", "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -1071,7 +1106,9 @@ def run_latency(args):
             "config": {"workload": f"dependent chains: {ctas} CTAs x {threads} threads "
                                    "(loaded) or one warp", "hops_loaded": 200,
                        "hops_1warp": 2000},
-            "latency_ns": lat, "gpu_launches": 24,
+            "latency_ns": lat, "random_gaccess_per_s": thr,
+            # each probe: array set-up, a warm-up launch and the timed launch
+            "gpu_launches": 3 * (len(lat) + len(thr)),
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
     print(json.dumps(line), flush=True)
 

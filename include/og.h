@@ -386,12 +386,14 @@ int og_launch_status(uint32_t err, uint32_t bad_code, uint32_t bad_val, uint32_t
  * two, 4 KiB .. bytes; every hop lands far from the previous one): footprint = bytes
  * touches the whole array, a small footprint spread over a large array stays in L2 but
  * spans many pages.  *ns_per_hop receives the kernel time / hops, i.e. the round-trip
- * time of one access with that many chains in flight.  mode 0: relaxed loads served by
- * L2; 1: atomicMin whose result is used (the array is left unchanged); 2: non-coherent
- * loads through L1.  Allocates and frees its array; synchronises the device.
- * OG_E_INVALID for bad sizes (threads a multiple of 32, at most 1024). */
+ * time of one access with that many chains in flight.  Each thread follows chains (1, 2,
+ * 4, 8 or 16) independent chains, so ctas x threads x chains / *ns_per_hop is the rate
+ * of independent random accesses.  mode 0: relaxed loads served by L2; 1: atomicMin
+ * whose result is used (the array is left unchanged); 2: non-coherent loads through L1.
+ * Allocates and frees its array; synchronises the device.  OG_E_INVALID for bad sizes
+ * (threads a multiple of 32, at most 1024) or another chain count. */
 int og_probe_chain(uint32_t mode, uint64_t bytes, uint64_t footprint, uint32_t ctas,
-                   uint32_t threads, uint32_t hops, double* ns_per_hop);
+                   uint32_t threads, uint32_t chains, uint32_t hops, double* ns_per_hop);
 const char* og_strerror(int code);
 const char* og_last_cuda_error(void);
 int og_version(void);

@@ -111,7 +111,7 @@ def lib():
             "og_version": (i32, []),
             "og_sssp_delta_noalloc": (i32, [vp, vp, u32, u64, u32, u32, vp, vp]),
             "og_launch_status": (i32, [u32, u32, u32, u32, u32]),
-            "og_probe_chain": (i32, [u32, u64, u64, u32, u32, u32, P(ctypes.c_double)]),
+            "og_probe_chain": (i32, [u32, u64, u64, u32, u32, u32, u32, P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -425,13 +425,13 @@ def launch_status(err: int, bad_code: int = 0, bad_val: int = 0, bad_aux: int = 
 
 
 def probe_chain(mode: int, nbytes: int, ctas: int, threads: int, hops: int,
-                footprint: int = 0) -> float:
+                footprint: int = 0, chains: int = 1) -> float:
     """ns per dependent access: mode 0 L2 loads, 1 atomicMin round trips, 2 L1 loads;
     footprint (default: the whole array) = bytes of 128-byte lines the chains visit,
-    spread evenly over the nbytes array."""
+    spread evenly over the nbytes array; chains = independent chains per thread."""
     v = ctypes.c_double(0.0)
-    _check(lib().og_probe_chain(mode, nbytes, footprint or nbytes, ctas, threads, hops,
-                                ctypes.byref(v)), "og_probe_chain")
+    _check(lib().og_probe_chain(mode, nbytes, footprint or nbytes, ctas, threads, chains,
+                                hops, ctypes.byref(v)), "og_probe_chain")
     return float(v.value)
 
 

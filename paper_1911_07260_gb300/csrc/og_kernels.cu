@@ -168,10 +168,6 @@ __device__ __forceinline__ void mark_warp(const Params& P, bool first, uint32_t 
   else report_bad(P.sync, 41u, v, q);  // more marks in one round than the list holds
 }
 
-// Relaxes up to K edges per lane: nd = g + w (saturating), atomicMin on dist[v]; an
-// improvement is inserted eagerly into bucket floor((nd + h) / Delta).  All K neighbor
-// loads are issued before any atomic and all K atomics before any insert, so a lane keeps
-// K independent memory operations in flight instead of paying one round trip per edge.
 // Relaxes up to K already-loaded edges per lane: nd = g + w (saturating), atomicMin on
 // dist[v]; an improvement is inserted eagerly into bucket floor((nd + h) / Delta).  All K
 // atomics are issued before any insert, so a lane keeps K independent memory operations

@@ -10,7 +10,9 @@
 // it over a large array (a large spacing) adds address-translation misses without cache
 // misses.  Run with one warp the chains see the unloaded latency; run at the persistent
 // kernels' occupancy they see the latency under that many requests in flight, which is
-// what a fused level of the search waits for on each of its dependent steps.
+// what a fused level of the search waits for on each of its dependent steps.  With
+// several chains per thread the same kernel measures how many independent random
+// accesses a second the memory system serves (threads x chains / time per hop).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,33 +31,56 @@ __global__ void og_probe_init_kernel(uint32_t* buf, uint32_t lmask, uint32_t str
 
 // mode 0: ld.relaxed.gpu (served by L2), 1: atomicMin with the result used (an L2
 // atomic round trip; the value written is never smaller, so the array is unchanged),
-// 2: non-coherent load through L1 (__ldg).
-template <int MODE>
+// 2: non-coherent load through L1 (__ldg).  Each thread follows W independent chains,
+// so W accesses of a thread are in flight together.
+template <int MODE, int W>
 __global__ void og_probe_chain_kernel(uint32_t* buf, uint32_t lmask, uint32_t spacing_w,
                                       uint32_t hops, uint32_t* sink) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t i = ((t * 40961u) & lmask) * spacing_w;  // starting points on different lines
+  uint32_t i[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k)  // starting points on different lines
+    i[k] = (((t * W + k) * 40961u) & lmask) * spacing_w;
   for (uint32_t h = 0; h < hops; ++h) {
-    if (MODE == 0) {
-      asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(i) : "l"(buf + i) : "memory");
-    } else if (MODE == 1) {
-      i = atomicMin(buf + i, 0xFFFFFFFFu);
-    } else {
-      i = __ldg(buf + i);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      if (MODE == 0) {
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(i[k]) : "l"(buf + i[k]) : "memory");
+      } else if (MODE == 1) {
+        i[k] = atomicMin(buf + i[k], 0xFFFFFFFFu);
+      } else {
+        i[k] = __ldg(buf + i[k]);
+      }
     }
   }
-  if (i == 0xFFFFFFFFu) *sink = t;  // never true: keeps the chain live
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) x |= i[k];
+  if (x == 0xFFFFFFFFu) *sink = t;  // never true: keeps the chains live
+}
+
+template <int MODE>
+void launch_probe(uint32_t chains, uint32_t ctas, uint32_t threads, uint32_t* buf,
+                  uint32_t lmask, uint32_t spacing_w, uint32_t hops, uint32_t* sink) {
+  switch (chains) {
+    case 1: og_probe_chain_kernel<MODE, 1><<<ctas, threads>>>(buf, lmask, spacing_w, hops, sink); break;
+    case 2: og_probe_chain_kernel<MODE, 2><<<ctas, threads>>>(buf, lmask, spacing_w, hops, sink); break;
+    case 4: og_probe_chain_kernel<MODE, 4><<<ctas, threads>>>(buf, lmask, spacing_w, hops, sink); break;
+    case 8: og_probe_chain_kernel<MODE, 8><<<ctas, threads>>>(buf, lmask, spacing_w, hops, sink); break;
+    default: og_probe_chain_kernel<MODE, 16><<<ctas, threads>>>(buf, lmask, spacing_w, hops, sink); break;
+  }
 }
 
 }  // namespace og
 
 extern "C" int og_probe_chain(uint32_t mode, uint64_t bytes, uint64_t footprint,
-                              uint32_t ctas, uint32_t threads, uint32_t hops,
-                              double* ns_per_hop) {
+                              uint32_t ctas, uint32_t threads, uint32_t chains,
+                              uint32_t hops, double* ns_per_hop) {
   using namespace og;
   if (!ns_per_hop || mode > 2 || bytes < 4096 || (bytes & (bytes - 1)) || bytes > (16ull << 30) ||
       footprint < 4096 || (footprint & (footprint - 1)) || footprint > bytes || ctas == 0 ||
-      threads == 0 || threads > 1024 || threads % 32 || hops == 0)
+      threads == 0 || threads > 1024 || threads % 32 || hops == 0 ||
+      (chains != 1 && chains != 2 && chains != 4 && chains != 8 && chains != 16))
     return OG_E_INVALID;
   const uint64_t words = bytes / 4;
   const uint64_t lines = footprint / 128;
@@ -68,9 +93,9 @@ extern "C" int og_probe_chain(uint32_t mode, uint64_t bytes, uint64_t footprint,
   int rc = OG_OK;
   float ms = 0.f;
   auto launch = [&](uint32_t h) {
-    if (mode == 0) og_probe_chain_kernel<0><<<ctas, threads>>>(buf, lmask, spacing_w, h, sink);
-    else if (mode == 1) og_probe_chain_kernel<1><<<ctas, threads>>>(buf, lmask, spacing_w, h, sink);
-    else og_probe_chain_kernel<2><<<ctas, threads>>>(buf, lmask, spacing_w, h, sink);
+    if (mode == 0) launch_probe<0>(chains, ctas, threads, buf, lmask, spacing_w, h, sink);
+    else if (mode == 1) launch_probe<1>(chains, ctas, threads, buf, lmask, spacing_w, h, sink);
+    else launch_probe<2>(chains, ctas, threads, buf, lmask, spacing_w, h, sink);
   };
   if (cudaMalloc(&buf, words * 4) != cudaSuccess || cudaMalloc(&sink, 4) != cudaSuccess) {
     rc = OG_E_OOM;
