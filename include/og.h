@@ -167,8 +167,10 @@ typedef struct og_query {
  * integer weights).  offsets: host uint64[n+1], non-decreasing, offsets[0] = 0,
  * offsets[n] = m < 2^32.  neighbors, weights: host uint32[m]; the out-edges of u are
  * neighbors[offsets[u] .. offsets[u+1]) with the matching weights.  The library keeps
- * its own copy (uint32 offsets, interleaved {neighbor, weight} pairs).  Returns
- * OG_E_INVALID for n = 0, bad offsets or a neighbor >= n. */
+ * its own copy (uint32 offsets, interleaved {neighbor, weight} pairs).  A graph of at
+ * least 2^20 vertices whose n/8 highest-degree vertices hold half of the edges or more
+ * (a power-law graph) is stored hot-first (og_graph_set_order), if the device has the
+ * memory for the rebuild.  Returns OG_E_INVALID for n = 0, bad offsets or a neighbor >= n. */
 int og_graph_upload(const uint64_t* offsets, const uint32_t* neighbors,
                     const uint32_t* weights, uint32_t n, uint64_t m, void* stream,
                     og_graph** out);
@@ -178,6 +180,25 @@ int og_graph_upload(const uint64_t* offsets, const uint32_t* neighbors,
  * to the target; with integral coordinates below 2^24 it is computed exactly in
  * integers, otherwise as max(0, floor(100 * d) - 1) in double. */
 int og_graph_set_coords(og_graph* g, const float* xy, void* stream);
+
+/* Vertex order on the device (a layout choice; every result is the same).  Every search
+ * reads the distance of each relaxed edge's target at random, and on a power-law graph
+ * most of those reads hit a few high-degree vertices.  OG_ORDER_HOT_FIRST stores the n/8
+ * vertices of largest degree (ties: smaller id) at device ids [0, n/8), each swapped with
+ * a vertex that was there, so their distance words share cache lines that stay in L2;
+ * OG_ORDER_USER keeps the caller's ids; OG_ORDER_AUTO is the upload's rule above.  Ids
+ * and per-vertex arrays keep the caller's numbering at every call (sources, targets,
+ * coordinates, priorities, distances, coreness, join steps): the library maps them
+ * through the swaps.  The adjacency is rebuilt on the device (needs a second copy of it
+ * for the duration; OG_E_OOM leaves the graph as it was).  OG_E_BUSY while a server
+ * created on the graph exists; OG_E_INVALID for another order.  Synchronises stream. */
+#define OG_ORDER_AUTO 0u
+#define OG_ORDER_HOT_FIRST 1u
+#define OG_ORDER_USER 2u
+int og_graph_set_order(og_graph* g, uint32_t order, void* stream);
+/* The order in effect (OG_ORDER_HOT_FIRST or OG_ORDER_USER) and how many vertices have
+ * a device id other than their own (either pointer may be NULL). */
+int og_graph_get_order(const og_graph* g, uint32_t* order, uint32_t* moved);
 
 /* n, m, minimum and maximum edge weight (any pointer may be NULL). */
 int og_graph_info(const og_graph* g, uint32_t* n, uint64_t* m, uint32_t* min_w,

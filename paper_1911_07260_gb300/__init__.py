@@ -28,6 +28,7 @@ ENGINE_DEFAULT, ENGINE_ROUNDS, ENGINE_ASYNC = 0, 1, 2
 PRECHECK_ON, PRECHECK_OFF = 1, 2
 LAYOUT_CSR, LAYOUT_ELL = 1, 2
 PREFETCH_ON, PREFETCH_OFF = 1, 2
+ORDER_AUTO, ORDER_HOT_FIRST, ORDER_USER = 0, 1, 2
 KCORE_LAZY, KCORE_EAGER = 0, 1
 UPDATE_EAGER, UPDATE_LAZY = 1, 2
 UNREACHED = 0xFFFFFFFF
@@ -84,6 +85,8 @@ def lib():
         sig = {
             "og_graph_upload": (i32, [vp, vp, vp, u32, u64, vp, P(vp)]),
             "og_graph_set_coords": (i32, [vp, vp, vp]),
+            "og_graph_set_order": (i32, [vp, u32, vp]),
+            "og_graph_get_order": (i32, [vp, P(u32), P(u32)]),
             "og_graph_info": (i32, [vp, P(u32), P(u64), P(u32), P(u32)]),
             "og_graph_set_config": (i32, [vp, P(Config)]),
             "og_graph_get_config": (i32, [vp, P(Config)]),
@@ -212,6 +215,19 @@ class Graph:
             xy = np.ascontiguousarray(xy, dtype=np.float32)
         _check(lib().og_graph_set_coords(self.handle, _ptr(xy), _stream(stream)),
                "og_graph_set_coords")
+
+    def set_order(self, order: int, stream=None):
+        """Device vertex order: ORDER_AUTO, ORDER_HOT_FIRST or ORDER_USER (results keep
+        the caller's ids in every order)."""
+        _check(lib().og_graph_set_order(self.handle, order, _stream(stream)),
+               "og_graph_set_order")
+
+    def order(self) -> tuple:
+        """(order in effect, vertices whose device id differs from their own)."""
+        o, mv = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().og_graph_get_order(self.handle, ctypes.byref(o), ctypes.byref(mv)),
+               "og_graph_get_order")
+        return o.value, mv.value
 
     def info(self) -> dict:
         n, m, lo, hi = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libog.so")
 SOURCES = ["og_kernels.cu", "og_async.cu", "og_kcore.cu", "og_setcover.cu", "og_api.cu",
-           "og_probe.cu"]
+           "og_probe.cu", "og_order.cu"]
 HEADERS = [os.path.join(CSRC, "og_internal.cuh"), os.path.join(CSRC, "og_device.cuh"),
            os.path.join(CSRC, "og_kcore.cuh"),
            os.path.join(CSRC, "og_setcover.cuh"),

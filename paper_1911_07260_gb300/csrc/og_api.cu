@@ -51,6 +51,11 @@ cudaError_t launch_kcore_init(const uint32_t* off, uint32_t* prio, uint32_t n, i
 cudaError_t setcover_occupancy(int* blocks_per_sm);
 cudaError_t launch_setcover(const ScParams& P, int grid, cudaStream_t st);
 cudaError_t launch_setcover_prep(const ScParams& P, uint32_t* iota, int sms, cudaStream_t st);
+cudaError_t launch_pack_adj(const uint32_t* off_old, const uint2* adj_old,
+                            const uint32_t* off_new, const uint32_t* pi, uint2* adj_new,
+                            uint32_t n, int sms, cudaStream_t st);
+cudaError_t launch_swap_rows(uint32_t* rows, uint32_t n, uint32_t nrows, const uint2* swaps,
+                             uint32_t nswap, int sms, cudaStream_t st);
 }  // namespace og
 
 using namespace og;
@@ -215,6 +220,11 @@ constexpr uint32_t kSetcoverHub = 32;       // set cover: residual size of a lar
 constexpr int kSetcoverBps = 2;             // set cover: default CTAs per SM
 constexpr int kKcoreBps = 2;                // k-core: default CTAs per SM
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
+// Hot-first packing: the n / kHotDiv vertices of largest degree move to ids [0, n / kHotDiv)
+// when the graph has at least kHotMinN vertices and those vertices hold at least half of
+// the edges (a power-law degree distribution; a road network's top eighth holds ~15%).
+constexpr uint32_t kHotDiv = 8;
+constexpr uint32_t kHotMinN = 1u << 20;
 
 }  // namespace
 
@@ -239,6 +249,14 @@ struct og_graph {
   int occ_async = 0;
   int occ_l[2] = {0, 0};        // round engine: CTAs per SM for CSR / ELL
   int occ_async_l[2] = {0, 0};  // barrier-free engine
+  // Vertex order on the device.  Empty h_pi: the user's ids.  Otherwise device id x holds
+  // user vertex h_pi[x] (an involution made of the nswap transpositions in swaps), and
+  // every id crossing the boundary goes through h_pi, every per-vertex array through
+  // swaps (og_order.cu).
+  std::vector<uint32_t> h_pi;
+  uint2* swaps = nullptr;
+  uint32_t nswap = 0;
+  uint32_t servers = 0;         // live servers: their slots hold rows in the device order
 };
 
 struct og_server {
@@ -760,10 +778,144 @@ void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
   out->t_hub_ns = s.v[kStTHub];
 }
 
+// Device id of user vertex v (the graph's vertex order).
+uint32_t dev_id(const og_graph* g, uint32_t v) { return g->h_pi.empty() ? v : g->h_pi[v]; }
+
+// Maps nrows per-vertex rows of n words between the device order and the user's (the
+// same transpositions both ways); a no-op in the user's order.
+int swap_rows(const og_graph* g, uint32_t* rows, uint32_t nrows, cudaStream_t st) {
+  if (g->nswap == 0 || nrows == 0) return OG_OK;
+  CK(launch_swap_rows(rows, g->n, nrows, g->swaps, g->nswap, g->sms, st));
+  return OG_OK;
+}
+
+// Device copy of the coordinates in the device order (the host copy stays in the user's).
+int upload_coords(og_graph* g, cudaStream_t st) {
+  if (!g->xy || g->h_xy.empty()) return OG_OK;
+  std::vector<float> d;
+  const float* src = g->h_xy.data();
+  if (!g->h_pi.empty()) {
+    d.resize(g->h_xy.size());
+    for (uint32_t x = 0; x < g->n; ++x) {
+      d[2 * (size_t)x] = g->h_xy[2 * (size_t)g->h_pi[x]];
+      d[2 * (size_t)x + 1] = g->h_xy[2 * (size_t)g->h_pi[x] + 1];
+    }
+    src = d.data();
+  }
+  CK(cudaMemcpyAsync(g->xy, src, sizeof(float) * g->h_xy.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return OG_OK;
+}
+
+// The hot-first order of a graph whose vertices have degrees deg (in its current ids):
+// the K = n / kHotDiv vertices of largest degree (ties: the smaller id) take ids [0, K),
+// each outside that range swapped with a vertex inside it that is not among them, in
+// increasing order on both sides.  pi is the resulting involution; hot_edges the edges
+// the K vertices hold.
+void hot_first(const std::vector<uint32_t>& deg, std::vector<uint32_t>& pi,
+               std::vector<uint2>& swaps, uint64_t* hot_edges) {
+  const uint32_t n = (uint32_t)deg.size(), K = n / kHotDiv;
+  pi.resize(n);
+  for (uint32_t v = 0; v < n; ++v) pi[v] = v;
+  swaps.clear();
+  *hot_edges = 0;
+  if (K == 0) return;
+  std::vector<uint32_t> idx(pi);
+  std::nth_element(idx.begin(), idx.begin() + (K - 1), idx.end(), [&](uint32_t a, uint32_t b) {
+    return deg[a] != deg[b] ? deg[a] > deg[b] : a < b;
+  });
+  std::vector<char> hot(n, 0);
+  for (uint32_t i = 0; i < K; ++i) {
+    hot[idx[i]] = 1;
+    *hot_edges += deg[idx[i]];
+  }
+  uint32_t c = 0;  // next id below K that is not hot
+  for (uint32_t h = K; h < n; ++h) {
+    if (!hot[h]) continue;
+    while (hot[c]) ++c;  // as many cold ids below K as hot ids at or above it
+    pi[h] = c;
+    pi[c] = h;
+    swaps.push_back(make_uint2(c, h));
+    ++c;
+  }
+}
+
+// Puts the graph in the hot-first order (packed) or back in the user's.  The adjacency
+// and offsets are rebuilt on the device from the current ones (og_pack_adj_kernel), the
+// ELL rows and coordinates follow, and a transpose is dropped (rebuilt when asked for).
+// auto_mode packs only a large skewed graph.  OG_E_BUSY while a server uses the graph;
+// on OG_E_OOM the graph is unchanged.
+int set_order(og_graph* g, uint32_t order, cudaStream_t st) {
+  const uint32_t n = g->n;
+  const bool cur = !g->h_pi.empty();
+  std::vector<uint32_t> off(n + 1);
+  CK(cudaMemcpyAsync(off.data(), g->off, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<uint32_t> pi;
+  std::vector<uint2> sw;
+  bool want = order == OG_ORDER_HOT_FIRST;
+  if (order == OG_ORDER_AUTO || order == OG_ORDER_HOT_FIRST) {
+    if (cur) return OG_OK;  // already packed
+    std::vector<uint32_t> deg(n);
+    for (uint32_t v = 0; v < n; ++v) deg[v] = off[v + 1] - off[v];
+    uint64_t hot_edges = 0;
+    hot_first(deg, pi, sw, &hot_edges);
+    if (order == OG_ORDER_AUTO) want = n >= kHotMinN && 2 * hot_edges >= g->m;
+    if (!want || sw.empty()) return OG_OK;
+  } else {
+    if (!cur) return OG_OK;  // already in the user's order
+    pi = g->h_pi;
+  }
+  if (g->servers) return OG_E_BUSY;
+  std::vector<uint32_t> offn(n + 1);
+  offn[0] = 0;
+  for (uint32_t x = 0; x < n; ++x) offn[x + 1] = offn[x] + (off[pi[x] + 1] - off[pi[x]]);
+  uint32_t *d_off = nullptr, *d_pi = nullptr;
+  uint2 *d_adj = nullptr, *d_sw = nullptr;
+  auto undo = [&](int code) {
+    if (d_off) cudaFree(d_off);
+    if (d_pi) cudaFree(d_pi);
+    if (d_adj) cudaFree(d_adj);
+    if (d_sw) cudaFree(d_sw);
+    cudaGetLastError();
+    return code;
+  };
+  if (cudaMalloc(&d_off, sizeof(uint32_t) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&d_pi, sizeof(uint32_t) * n) != cudaSuccess ||
+      cudaMalloc(&d_adj, sizeof(uint2) * (g->m ? g->m : 1)) != cudaSuccess ||
+      (want && cudaMalloc(&d_sw, sizeof(uint2) * sw.size()) != cudaSuccess))
+    return undo(OG_E_OOM);
+  cudaError_t e = cudaMemcpyAsync(d_off, offn.data(), sizeof(uint32_t) * (n + 1),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_pi, pi.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && want)
+    e = cudaMemcpyAsync(d_sw, sw.data(), sizeof(uint2) * sw.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_pack_adj(g->off, g->adj, d_off, d_pi, d_adj, n, g->sms, st);
+  if (e == cudaSuccess && g->ell) e = launch_ell(d_off, d_adj, g->ell, n, g->sms, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return undo(cuda_fail(e, "vertex order"));
+  cudaFree(d_pi);
+  cudaFree(g->off);
+  cudaFree(g->adj);
+  g->off = d_off;
+  g->adj = d_adj;
+  if (g->toff) cudaFree(g->toff);
+  if (g->tadj) cudaFree(g->tadj);
+  g->toff = nullptr;
+  g->tadj = nullptr;
+  if (g->swaps) cudaFree(g->swaps);
+  g->swaps = want ? d_sw : nullptr;
+  g->nswap = want ? (uint32_t)sw.size() : 0u;
+  if (want) g->h_pi.swap(pi);
+  else g->h_pi.clear();
+  return upload_coords(g, st);
+}
+
 int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d) {
   if (q.src >= g->n) return OG_E_INVALID;
   memset(d, 0, sizeof(*d));
-  d->src = q.src;
+  d->src = dev_id(g, q.src);
   d->dst = kNone;
   switch (q.kind) {
     case OG_Q_SSSP:
@@ -780,8 +932,8 @@ int make_desc(const og_graph* g, const og_query& q, const og_config& c, QDesc* d
       if (q.dst >= g->n) return OG_E_INVALID;
       if (q.kind == OG_Q_ASTAR && !g->xy) return OG_E_INVALID;
       d->kind = q.kind == OG_Q_PPSP ? kPPSP : kASTAR;
-      d->dst = q.dst;
-      if (q.kind == OG_Q_ASTAR) {
+      d->dst = dev_id(g, q.dst);
+      if (q.kind == OG_Q_ASTAR) {  // host coordinates stay in the user's order
         d->tx = g->h_xy[2 * (size_t)q.dst];
         d->ty = g->h_xy[2 * (size_t)q.dst + 1];
       }
@@ -819,6 +971,7 @@ int run_queries(og_graph* g, const og_query* qv, uint32_t nq, const og_config* u
     }
     TRY(run_chunk(g, g->ws, qd.data() + base, k, c, ddist, d_out ? d_out + base : nullptr,
                   &acc, &ro, st));
+    if (dist_out) TRY(swap_rows(g, ddist, k, st));
     if (dist_out && !dev_out) {
       CK(cudaMemcpyAsync(dist_out + (size_t)base * g->n, ddist,
                          sizeof(uint32_t) * (size_t)k * g->n, cudaMemcpyDeviceToHost, st));
@@ -939,6 +1092,12 @@ int og_graph_upload(const uint64_t* offsets, const uint32_t* neighbors, const ui
   g->cfg.fusion_threshold = 0;
   g->cfg.expand_tile = 0;
   g->cfg.spin_limit_ns = 0;
+  if (m) {
+    // A large power-law graph is packed hot-first; without the memory for the rebuild it
+    // stays in the user's order.
+    const int rc = set_order(g, OG_ORDER_AUTO, st);
+    if (rc != OG_OK && rc != OG_E_OOM) return fail(rc);
+  }
   *out = g;
   return OG_OK;
 }
@@ -965,10 +1124,21 @@ int og_graph_set_coords(og_graph* g, const float* xy, void* stream) {
       return cuda_fail(e, "cudaMalloc coords");
     }
   }
-  CK(cudaMemcpyAsync(g->xy, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));
   g->xy_integral = integral;
   g->h_xy.swap(h);
+  return upload_coords(g, st);
+}
+
+int og_graph_set_order(og_graph* g, uint32_t order, void* stream) {
+  if (!g || order > OG_ORDER_USER) return OG_E_INVALID;
+  if (!g->m) return OG_OK;
+  return set_order(g, order, (cudaStream_t)stream);
+}
+
+int og_graph_get_order(const og_graph* g, uint32_t* order, uint32_t* moved) {
+  if (!g) return OG_E_INVALID;
+  if (order) *order = g->h_pi.empty() ? OG_ORDER_USER : OG_ORDER_HOT_FIRST;
+  if (moved) *moved = 2 * g->nswap;
   return OG_OK;
 }
 
@@ -1003,6 +1173,7 @@ void og_graph_free(og_graph* g) {
   if (g->xy) cudaFree(g->xy);
   if (g->toff) cudaFree(g->toff);
   if (g->tadj) cudaFree(g->tadj);
+  if (g->swaps) cudaFree(g->swaps);
   delete g;
 }
 
@@ -1124,6 +1295,7 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   CK(cudaMemcpyAsync(ws.h_sync.p, P.sync, sizeof(Sync), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_stats.p, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_kstate.p, P.ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  TRY(swap_rows(g, prio, 1, st));
   if (!dev_out)
     CK(cudaMemcpyAsync(core_out, prio, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1189,7 +1361,10 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   // band lists: each set enters each band at most once, sum (first band + 1) <= n + m/16
   const uint64_t bl_entries = 2ull * ((uint64_t)n + m / kScBand + nbands + 1);
   const bool dev_out = is_device_ptr(step_out);
-  const bool dev_pri = priority && is_device_ptr(priority);
+  // In a packed vertex order the priorities are staged in the workspace and permuted
+  // there; the caller's buffer is never written.
+  const bool packed = g->nswap != 0;
+  const bool dev_pri = priority && is_device_ptr(priority) && !packed;
   TRY(ws.sclad.ensure(sizeof(uint32_t) * lad.size()));
   TRY(ws.sclen.ensure(sizeof(uint32_t) * (size_t)n));
   TRY(ws.scpk.ensure(2 * sizeof(uint32_t) * (size_t)std::max<uint64_t>(m, 1)));
@@ -1255,19 +1430,26 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
                      cudaMemcpyHostToDevice, st));
   if (priority && !dev_pri)
     CK(cudaMemcpyAsync(ws.scpri.p, priority, sizeof(uint32_t) * (size_t)n,
+                       cudaMemcpyDefault, st));
+  if (packed && !priority)  // the identity in user ids is pi in device ids
+    CK(cudaMemcpyAsync(ws.scpri.p, g->h_pi.data(), sizeof(uint32_t) * (size_t)n,
                        cudaMemcpyHostToDevice, st));
+  else if (packed)
+    TRY(swap_rows(g, ws.scpri.as<uint32_t>(), 1, st));
   CK(cudaMemsetAsync(meta, 0, 5 * sizeof(uint32_t) * (size_t)nbm, st));
   CK(cudaMemsetAsync(P.seen, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), st));
   CK(cudaMemsetAsync(P.ss, 0, sizeof(ScState), st));
   CK(cudaMemsetAsync(P.sync, 0, sizeof(Sync), st));
   CK(cudaMemsetAsync(P.stats, 0, sizeof(Stats), st));
   CK(cudaEventRecord(ws.e0, st));
-  CK(launch_setcover_prep(P, priority ? nullptr : ws.scpri.as<uint32_t>(), g->sms, st));
+  CK(launch_setcover_prep(P, (priority || packed) ? nullptr : ws.scpri.as<uint32_t>(), g->sms,
+                          st));
   CK(launch_setcover(P, g->sms * bps, st));
   CK(cudaEventRecord(ws.e1, st));
   CK(cudaMemcpyAsync(ws.h_sync.p, P.sync, sizeof(Sync), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_stats.p, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_kstate.p, P.ss, sizeof(ScState), cudaMemcpyDeviceToHost, st));
+  TRY(swap_rows(g, P.step_out, 1, st));
   if (!dev_out)
     CK(cudaMemcpyAsync(step_out, P.step_out, sizeof(uint32_t) * (size_t)n,
                        cudaMemcpyDeviceToHost, st));
@@ -1283,7 +1465,8 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   if (hy->err & kErrBounds) {
     if (hy->bad_code == kScBadPriority) {
       snprintf(g_cuda_msg, sizeof(g_cuda_msg),
-               "priority of set %u (%u) is out of range or repeated", hy->bad_val, hy->bad_aux);
+               "priority of set %u (%u) is out of range or repeated",
+               hy->bad_val < n ? dev_id(g, hy->bad_val) : hy->bad_val, hy->bad_aux);
       return OG_E_INVALID;
     }
     snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",
@@ -1416,6 +1599,7 @@ int og_server_create(og_graph* g, uint32_t max_slots, const og_config* cfg, void
   s->state.assign(slots, 0);
   s->results.assign(slots, kInf);
   for (uint32_t i = slots; i > 0; --i) s->free_list.push_back(i - 1);
+  s->g->servers++;
   *out = s;
   return OG_OK;
 }
@@ -1563,6 +1747,7 @@ int og_server_slots(const og_server* s, uint32_t* max_slots, uint32_t* n_free) {
 void og_server_free(og_server* s) {
   if (!s) return;
   s->ws.release();
+  if (s->g && s->g->servers) s->g->servers--;
   delete s;
 }
 
