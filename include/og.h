@@ -184,20 +184,21 @@ int og_graph_set_coords(og_graph* g, const float* xy, void* stream);
 /* Vertex order on the device (a layout choice; every result is the same).  Every search
  * reads the distance of each relaxed edge's target at random, and on a power-law graph
  * most of those reads hit a few high-degree vertices.  OG_ORDER_HOT_FIRST stores the n/8
- * vertices of largest degree (ties: smaller id) at device ids [0, n/8), each swapped with
- * a vertex that was there, so their distance words share cache lines that stay in L2;
- * OG_ORDER_USER keeps the caller's ids; OG_ORDER_AUTO is the upload's rule above.  Ids
- * and per-vertex arrays keep the caller's numbering at every call (sources, targets,
- * coordinates, priorities, distances, coreness, join steps): the library maps them
- * through the swaps.  The adjacency is rebuilt on the device (needs a second copy of it
- * for the duration; OG_E_OOM leaves the graph as it was).  OG_E_BUSY while a server
- * created on the graph exists; OG_E_INVALID for another order.  Synchronises stream. */
+ * vertices of largest degree (ties: smaller id) at device ids 0 .. n/8 - 1 in that order,
+ * and the vertices they displace at the ids they left, so the hot distance words share
+ * cache lines that stay in L2; OG_ORDER_USER keeps the caller's ids; OG_ORDER_AUTO is the
+ * upload's rule above.  Ids and per-vertex arrays keep the caller's numbering at every
+ * call (sources, targets, coordinates, priorities, distances, coreness, join steps): the
+ * library maps them, touching only the moved vertices.  The adjacency is rebuilt on the
+ * device (needs a second copy of it for the duration; OG_E_OOM leaves the graph as it
+ * was).  OG_E_BUSY while a server created on the graph exists; OG_E_INVALID for another
+ * order.  Synchronises stream. */
 #define OG_ORDER_AUTO 0u
 #define OG_ORDER_HOT_FIRST 1u
 #define OG_ORDER_USER 2u
 int og_graph_set_order(og_graph* g, uint32_t order, void* stream);
 /* The order in effect (OG_ORDER_HOT_FIRST or OG_ORDER_USER) and how many vertices have
- * a device id other than their own (either pointer may be NULL). */
+ * a device id other than their own id (either pointer may be NULL). */
 int og_graph_get_order(const og_graph* g, uint32_t* order, uint32_t* moved);
 
 /* n, m, minimum and maximum edge weight (any pointer may be NULL). */

@@ -52,10 +52,12 @@ cudaError_t setcover_occupancy(int* blocks_per_sm);
 cudaError_t launch_setcover(const ScParams& P, int grid, cudaStream_t st);
 cudaError_t launch_setcover_prep(const ScParams& P, uint32_t* iota, int sms, cudaStream_t st);
 cudaError_t launch_pack_adj(const uint32_t* off_old, const uint2* adj_old,
-                            const uint32_t* off_new, const uint32_t* pi, uint2* adj_new,
-                            uint32_t n, int sms, cudaStream_t st);
-cudaError_t launch_swap_rows(uint32_t* rows, uint32_t n, uint32_t nrows, const uint2* swaps,
-                             uint32_t nswap, int sms, cudaStream_t st);
+                            const uint32_t* off_new, const uint32_t* src_of,
+                            const uint32_t* new_of, uint2* adj_new, uint32_t n, int sms,
+                            cudaStream_t st);
+cudaError_t launch_perm_rows(uint32_t* rows, uint32_t n, uint32_t nrows, const uint2* mv,
+                             uint32_t nmv, bool to_user, uint32_t* tmp, int sms,
+                             cudaStream_t st);
 }  // namespace og
 
 using namespace og;
@@ -152,6 +154,7 @@ struct HBuf {
 struct Workspace {
   DBuf dist, ring, counts, ovf, qs, qd, pref, sync, stats, slots, aq, big, bmap;
   DBuf stouched;  // server: touched-block bitmaps of the slots' distance rows
+  DBuf permtmp;   // staging of the moved entries when rows change vertex order
   DBuf kprio, kcnt, ktouched, klist, kring, kcounts, klossy, kstate;  // k-core
   DBuf lzbits, lzlist;  // lazy bucket update
   DBuf sclad, sclen, scpk, sccov, scclaim, scseen, scmeta, scbase, scbl, scsm, sclg, scstate,
@@ -165,7 +168,7 @@ struct Workspace {
   void* ring_ptr = nullptr;
   void release() {
     for (DBuf* b : {&dist, &ring, &counts, &ovf, &qs, &qd, &pref, &sync, &stats, &slots, &aq,
-                    &stouched, &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
+                    &stouched, &permtmp, &big, &bmap, &kprio, &kcnt, &ktouched, &klist, &kring, &kcounts, &klossy,
                     &kstate, &lzbits, &lzlist, &sclad, &sclen, &scpk, &sccov, &scclaim, &scseen,
                     &scmeta, &scbase, &scbl, &scsm, &sclg, &scstate, &scpri, &scout})
       b->release();
@@ -220,9 +223,10 @@ constexpr uint32_t kSetcoverHub = 32;       // set cover: residual size of a lar
 constexpr int kSetcoverBps = 2;             // set cover: default CTAs per SM
 constexpr int kKcoreBps = 2;                // k-core: default CTAs per SM
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
-// Hot-first packing: the n / kHotDiv vertices of largest degree move to ids [0, n / kHotDiv)
-// when the graph has at least kHotMinN vertices and those vertices hold at least half of
-// the edges (a power-law degree distribution; a road network's top eighth holds ~15%).
+// Hot-first packing: the n / kHotDiv vertices of largest degree move to ids [0, n / kHotDiv),
+// in order of degree, when the graph has at least kHotMinN vertices and those vertices
+// hold at least half of the edges (a power-law degree distribution; a road network's top
+// eighth holds ~15%).
 constexpr uint32_t kHotDiv = 8;
 constexpr uint32_t kHotMinN = 1u << 20;
 
@@ -250,12 +254,12 @@ struct og_graph {
   int occ_l[2] = {0, 0};        // round engine: CTAs per SM for CSR / ELL
   int occ_async_l[2] = {0, 0};  // barrier-free engine
   // Vertex order on the device.  Empty h_pi: the user's ids.  Otherwise device id x holds
-  // user vertex h_pi[x] (an involution made of the nswap transpositions in swaps), and
-  // every id crossing the boundary goes through h_pi, every per-vertex array through
-  // swaps (og_order.cu).
-  std::vector<uint32_t> h_pi;
-  uint2* swaps = nullptr;
-  uint32_t nswap = 0;
+  // user vertex h_pi[x] and user vertex v has device id h_dev[v]; every id crossing the
+  // boundary goes through them, every per-vertex array through the moved list mv
+  // ({device id, user id} of the nmv vertices whose ids differ; og_order.cu).
+  std::vector<uint32_t> h_pi, h_dev;
+  uint2* mv = nullptr;
+  uint32_t nmv = 0;
   uint32_t servers = 0;         // live servers: their slots hold rows in the device order
 };
 
@@ -778,14 +782,18 @@ void export_stats(const Stats& s, uint64_t restarts, og_stats* out) {
   out->t_hub_ns = s.v[kStTHub];
 }
 
-// Device id of user vertex v (the graph's vertex order).
-uint32_t dev_id(const og_graph* g, uint32_t v) { return g->h_pi.empty() ? v : g->h_pi[v]; }
+// Device id of user vertex v, and user id of device vertex x (the graph's vertex order).
+uint32_t dev_id(const og_graph* g, uint32_t v) { return g->h_dev.empty() ? v : g->h_dev[v]; }
+uint32_t user_id(const og_graph* g, uint32_t x) { return g->h_pi.empty() ? x : g->h_pi[x]; }
 
-// Maps nrows per-vertex rows of n words between the device order and the user's (the
-// same transpositions both ways); a no-op in the user's order.
-int swap_rows(const og_graph* g, uint32_t* rows, uint32_t nrows, cudaStream_t st) {
-  if (g->nswap == 0 || nrows == 0) return OG_OK;
-  CK(launch_swap_rows(rows, g->n, nrows, g->swaps, g->nswap, g->sms, st));
+// Brings nrows per-vertex rows of n words (device memory) from the device order to the
+// user's (to_user) or back; a no-op in the user's order.
+int perm_rows(og_graph* g, Workspace& ws, uint32_t* rows, uint32_t nrows, bool to_user,
+              cudaStream_t st) {
+  if (g->nmv == 0 || nrows == 0) return OG_OK;
+  TRY(ws.permtmp.ensure(sizeof(uint32_t) * (size_t)g->nmv * nrows));
+  CK(launch_perm_rows(rows, g->n, nrows, g->mv, g->nmv, to_user, ws.permtmp.as<uint32_t>(),
+                      g->sms, st));
   return OG_OK;
 }
 
@@ -807,95 +815,110 @@ int upload_coords(og_graph* g, cudaStream_t st) {
   return OG_OK;
 }
 
-// The hot-first order of a graph whose vertices have degrees deg (in its current ids):
-// the K = n / kHotDiv vertices of largest degree (ties: the smaller id) take ids [0, K),
-// each outside that range swapped with a vertex inside it that is not among them, in
-// increasing order on both sides.  pi is the resulting involution; hot_edges the edges
-// the K vertices hold.
+// The hot-first order of a graph in the user's ids with degrees deg: the K = n / kHotDiv
+// vertices of largest degree (ties: the smaller id) take device ids 0, 1, ..., K - 1 in
+// that order, and the other vertices below K take the ids the hot vertices left, in
+// increasing order on both sides.  pi[x] = user vertex at device id x, dev = its inverse;
+// hot_edges = the edges the K vertices hold.
 void hot_first(const std::vector<uint32_t>& deg, std::vector<uint32_t>& pi,
-               std::vector<uint2>& swaps, uint64_t* hot_edges) {
+               std::vector<uint32_t>& dev, uint64_t* hot_edges) {
   const uint32_t n = (uint32_t)deg.size(), K = n / kHotDiv;
   pi.resize(n);
+  dev.resize(n);
   for (uint32_t v = 0; v < n; ++v) pi[v] = v;
-  swaps.clear();
   *hot_edges = 0;
-  if (K == 0) return;
+  if (K == 0) {
+    dev = pi;
+    return;
+  }
   std::vector<uint32_t> idx(pi);
-  std::nth_element(idx.begin(), idx.begin() + (K - 1), idx.end(), [&](uint32_t a, uint32_t b) {
-    return deg[a] != deg[b] ? deg[a] > deg[b] : a < b;
-  });
+  auto hotter = [&](uint32_t a, uint32_t b) { return deg[a] != deg[b] ? deg[a] > deg[b] : a < b; };
+  std::nth_element(idx.begin(), idx.begin() + (K - 1), idx.end(), hotter);
+  std::sort(idx.begin(), idx.begin() + K, hotter);
   std::vector<char> hot(n, 0);
   for (uint32_t i = 0; i < K; ++i) {
     hot[idx[i]] = 1;
     *hot_edges += deg[idx[i]];
   }
+  for (uint32_t i = 0; i < K; ++i) pi[i] = idx[i];
   uint32_t c = 0;  // next id below K that is not hot
   for (uint32_t h = K; h < n; ++h) {
-    if (!hot[h]) continue;
-    while (hot[c]) ++c;  // as many cold ids below K as hot ids at or above it
-    pi[h] = c;
-    pi[c] = h;
-    swaps.push_back(make_uint2(c, h));
-    ++c;
+    if (!hot[h]) continue;  // pi[h] = h already
+    while (hot[c]) ++c;     // as many such ids below K as hot ids at or above it
+    pi[h] = c++;
   }
+  for (uint32_t x = 0; x < n; ++x) dev[pi[x]] = x;
 }
 
 // Puts the graph in the hot-first order (packed) or back in the user's.  The adjacency
 // and offsets are rebuilt on the device from the current ones (og_pack_adj_kernel), the
 // ELL rows and coordinates follow, and a transpose is dropped (rebuilt when asked for).
-// auto_mode packs only a large skewed graph.  OG_E_BUSY while a server uses the graph;
-// on OG_E_OOM the graph is unchanged.
+// OG_ORDER_AUTO packs only a large skewed graph.  OG_E_BUSY while a server uses the
+// graph; on OG_E_OOM the graph is unchanged.
 int set_order(og_graph* g, uint32_t order, cudaStream_t st) {
   const uint32_t n = g->n;
   const bool cur = !g->h_pi.empty();
+  const bool pack = order != OG_ORDER_USER;
+  if (pack == cur) return OG_OK;  // hot-first (of the same graph) or the user's already
   std::vector<uint32_t> off(n + 1);
   CK(cudaMemcpyAsync(off.data(), g->off, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  std::vector<uint32_t> pi;
-  std::vector<uint2> sw;
-  bool want = order == OG_ORDER_HOT_FIRST;
-  if (order == OG_ORDER_AUTO || order == OG_ORDER_HOT_FIRST) {
-    if (cur) return OG_OK;  // already packed
+  // src_of[x]: current id of the vertex that gets new id x; new_of: current id -> new id.
+  std::vector<uint32_t> pi, dev;
+  std::vector<uint2> mv;
+  const std::vector<uint32_t>* src_of;
+  const std::vector<uint32_t>* new_of;
+  if (pack) {
     std::vector<uint32_t> deg(n);
     for (uint32_t v = 0; v < n; ++v) deg[v] = off[v + 1] - off[v];
     uint64_t hot_edges = 0;
-    hot_first(deg, pi, sw, &hot_edges);
-    if (order == OG_ORDER_AUTO) want = n >= kHotMinN && 2 * hot_edges >= g->m;
-    if (!want || sw.empty()) return OG_OK;
+    hot_first(deg, pi, dev, &hot_edges);
+    if (order == OG_ORDER_AUTO && !(n >= kHotMinN && 2 * hot_edges >= g->m)) return OG_OK;
+    for (uint32_t x = 0; x < n; ++x)
+      if (pi[x] != x) mv.push_back(make_uint2(x, pi[x]));
+    if (mv.empty()) return OG_OK;  // the user's order is hot-first already
+    src_of = &pi;
+    new_of = &dev;
   } else {
-    if (!cur) return OG_OK;  // already in the user's order
-    pi = g->h_pi;
+    src_of = &g->h_dev;
+    new_of = &g->h_pi;
   }
   if (g->servers) return OG_E_BUSY;
   std::vector<uint32_t> offn(n + 1);
   offn[0] = 0;
-  for (uint32_t x = 0; x < n; ++x) offn[x + 1] = offn[x] + (off[pi[x] + 1] - off[pi[x]]);
-  uint32_t *d_off = nullptr, *d_pi = nullptr;
-  uint2 *d_adj = nullptr, *d_sw = nullptr;
+  for (uint32_t x = 0; x < n; ++x) {
+    const uint32_t u = (*src_of)[x];
+    offn[x + 1] = offn[x] + (off[u + 1] - off[u]);
+  }
+  uint32_t *d_off = nullptr, *d_src = nullptr, *d_new = nullptr;
+  uint2 *d_adj = nullptr, *d_mv = nullptr;
   auto undo = [&](int code) {
-    if (d_off) cudaFree(d_off);
-    if (d_pi) cudaFree(d_pi);
-    if (d_adj) cudaFree(d_adj);
-    if (d_sw) cudaFree(d_sw);
+    for (void* p : {(void*)d_off, (void*)d_src, (void*)d_new, (void*)d_adj, (void*)d_mv})
+      if (p) cudaFree(p);
     cudaGetLastError();
     return code;
   };
   if (cudaMalloc(&d_off, sizeof(uint32_t) * (n + 1)) != cudaSuccess ||
-      cudaMalloc(&d_pi, sizeof(uint32_t) * n) != cudaSuccess ||
+      cudaMalloc(&d_src, sizeof(uint32_t) * n) != cudaSuccess ||
+      cudaMalloc(&d_new, sizeof(uint32_t) * n) != cudaSuccess ||
       cudaMalloc(&d_adj, sizeof(uint2) * (g->m ? g->m : 1)) != cudaSuccess ||
-      (want && cudaMalloc(&d_sw, sizeof(uint2) * sw.size()) != cudaSuccess))
+      (pack && cudaMalloc(&d_mv, sizeof(uint2) * mv.size()) != cudaSuccess))
     return undo(OG_E_OOM);
   cudaError_t e = cudaMemcpyAsync(d_off, offn.data(), sizeof(uint32_t) * (n + 1),
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_pi, pi.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && want)
-    e = cudaMemcpyAsync(d_sw, sw.data(), sizeof(uint2) * sw.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = launch_pack_adj(g->off, g->adj, d_off, d_pi, d_adj, n, g->sms, st);
+    e = cudaMemcpyAsync(d_src, src_of->data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_new, new_of->data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && pack)
+    e = cudaMemcpyAsync(d_mv, mv.data(), sizeof(uint2) * mv.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_pack_adj(g->off, g->adj, d_off, d_src, d_new, d_adj, n, g->sms, st);
   if (e == cudaSuccess && g->ell) e = launch_ell(d_off, d_adj, g->ell, n, g->sms, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return undo(cuda_fail(e, "vertex order"));
-  cudaFree(d_pi);
+  cudaFree(d_src);
+  cudaFree(d_new);
   cudaFree(g->off);
   cudaFree(g->adj);
   g->off = d_off;
@@ -904,11 +927,16 @@ int set_order(og_graph* g, uint32_t order, cudaStream_t st) {
   if (g->tadj) cudaFree(g->tadj);
   g->toff = nullptr;
   g->tadj = nullptr;
-  if (g->swaps) cudaFree(g->swaps);
-  g->swaps = want ? d_sw : nullptr;
-  g->nswap = want ? (uint32_t)sw.size() : 0u;
-  if (want) g->h_pi.swap(pi);
-  else g->h_pi.clear();
+  if (g->mv) cudaFree(g->mv);
+  g->mv = pack ? d_mv : nullptr;
+  g->nmv = pack ? (uint32_t)mv.size() : 0u;
+  if (pack) {
+    g->h_pi.swap(pi);
+    g->h_dev.swap(dev);
+  } else {
+    g->h_pi.clear();
+    g->h_dev.clear();
+  }
   return upload_coords(g, st);
 }
 
@@ -971,7 +999,7 @@ int run_queries(og_graph* g, const og_query* qv, uint32_t nq, const og_config* u
     }
     TRY(run_chunk(g, g->ws, qd.data() + base, k, c, ddist, d_out ? d_out + base : nullptr,
                   &acc, &ro, st));
-    if (dist_out) TRY(swap_rows(g, ddist, k, st));
+    if (dist_out) TRY(perm_rows(g, g->ws, ddist, k, true, st));
     if (dist_out && !dev_out) {
       CK(cudaMemcpyAsync(dist_out + (size_t)base * g->n, ddist,
                          sizeof(uint32_t) * (size_t)k * g->n, cudaMemcpyDeviceToHost, st));
@@ -1138,7 +1166,7 @@ int og_graph_set_order(og_graph* g, uint32_t order, void* stream) {
 int og_graph_get_order(const og_graph* g, uint32_t* order, uint32_t* moved) {
   if (!g) return OG_E_INVALID;
   if (order) *order = g->h_pi.empty() ? OG_ORDER_USER : OG_ORDER_HOT_FIRST;
-  if (moved) *moved = 2 * g->nswap;
+  if (moved) *moved = g->nmv;
   return OG_OK;
 }
 
@@ -1173,7 +1201,7 @@ void og_graph_free(og_graph* g) {
   if (g->xy) cudaFree(g->xy);
   if (g->toff) cudaFree(g->toff);
   if (g->tadj) cudaFree(g->tadj);
-  if (g->swaps) cudaFree(g->swaps);
+  if (g->mv) cudaFree(g->mv);
   delete g;
 }
 
@@ -1295,7 +1323,7 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   CK(cudaMemcpyAsync(ws.h_sync.p, P.sync, sizeof(Sync), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_stats.p, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_kstate.p, P.ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
-  TRY(swap_rows(g, prio, 1, st));
+  TRY(perm_rows(g, ws, prio, 1, true, st));
   if (!dev_out)
     CK(cudaMemcpyAsync(core_out, prio, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1363,7 +1391,7 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   const bool dev_out = is_device_ptr(step_out);
   // In a packed vertex order the priorities are staged in the workspace and permuted
   // there; the caller's buffer is never written.
-  const bool packed = g->nswap != 0;
+  const bool packed = g->nmv != 0;
   const bool dev_pri = priority && is_device_ptr(priority) && !packed;
   TRY(ws.sclad.ensure(sizeof(uint32_t) * lad.size()));
   TRY(ws.sclen.ensure(sizeof(uint32_t) * (size_t)n));
@@ -1435,7 +1463,7 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
     CK(cudaMemcpyAsync(ws.scpri.p, g->h_pi.data(), sizeof(uint32_t) * (size_t)n,
                        cudaMemcpyHostToDevice, st));
   else if (packed)
-    TRY(swap_rows(g, ws.scpri.as<uint32_t>(), 1, st));
+    TRY(perm_rows(g, ws, ws.scpri.as<uint32_t>(), 1, false, st));
   CK(cudaMemsetAsync(meta, 0, 5 * sizeof(uint32_t) * (size_t)nbm, st));
   CK(cudaMemsetAsync(P.seen, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), st));
   CK(cudaMemsetAsync(P.ss, 0, sizeof(ScState), st));
@@ -1449,7 +1477,7 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   CK(cudaMemcpyAsync(ws.h_sync.p, P.sync, sizeof(Sync), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_stats.p, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ws.h_kstate.p, P.ss, sizeof(ScState), cudaMemcpyDeviceToHost, st));
-  TRY(swap_rows(g, P.step_out, 1, st));
+  TRY(perm_rows(g, ws, P.step_out, 1, true, st));
   if (!dev_out)
     CK(cudaMemcpyAsync(step_out, P.step_out, sizeof(uint32_t) * (size_t)n,
                        cudaMemcpyDeviceToHost, st));
@@ -1466,7 +1494,7 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
     if (hy->bad_code == kScBadPriority) {
       snprintf(g_cuda_msg, sizeof(g_cuda_msg),
                "priority of set %u (%u) is out of range or repeated",
-               hy->bad_val < n ? dev_id(g, hy->bad_val) : hy->bad_val, hy->bad_aux);
+               hy->bad_val < n ? user_id(g, hy->bad_val) : hy->bad_val, hy->bad_aux);
       return OG_E_INVALID;
     }
     snprintf(g_cuda_msg, sizeof(g_cuda_msg), "check %u failed: value %u, context %u",

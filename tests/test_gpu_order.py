@@ -152,8 +152,8 @@ def test_order_server_and_busy(og, orc, gg):
 
 
 def test_order_round_trip_and_auto(og, orc, gg):
-    """Hot-first and back gives the caller's order again (the swaps are an involution);
-    automatic order keeps a small graph as given and packs a large power-law one."""
+    """Hot-first and back gives the caller's order again; automatic order keeps a small
+    graph as given and packs a large power-law one."""
     g = gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1000, seed=5)
     G = og.Graph.from_csr(g)
     assert G.order() == (og.ORDER_USER, 0)         # below the automatic size
