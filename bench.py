@@ -84,6 +84,8 @@ def parse_args(argv=None):
     p.add_argument("--pull-divisor", type=int, default=0,
                    help="direction optimisation: pull a query's round when its frontier "
                         "exceeds n / this (0 = always push)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="road-sssp: skip the brief serve and R-MAT runs")
     p.add_argument("--no-batch", action="store_true",
                    help="default workload: skip the 256-query batch measurement")
     p.add_argument("--launch-check", action="store_true",
@@ -435,6 +437,19 @@ def run_ours(args):
     batch4 = None
     if args.workload == "road-sssp" and not args.no_batch and world == 1:
         batch4 = batch_measure(args, with_cpu=not args.no_cpu_baseline)
+    others = None
+    if args.workload == "road-sssp" and not args.no_configs and world == 1:
+        # the other benchmarked configurations in brief, on this machine in this run: served
+        # A*/PPSP on the same graph, then the R-MAT graph's wBFS and SSSP
+        serve = serve_measure(g, G, 5000, [20000.0], args.slots, args.budget_us,
+                              args.serve_fusion, 300)
+        others = {"serve": {"workload": f"{gname}, 5000 Poisson A*/PPSP queries offered at "
+                                        "20,000/s (saturating), continuous batching, "
+                                        f"{args.slots} slots",
+                            **{k: serve[k] for k in ("served", "one_at_a_time",
+                                                     "exact_served_eq_alone_eq_oracle")}},
+                  "rmat_wbfs": rmat_measure("rmat-wbfs", args.scale, 3),
+                  "rmat_sssp": rmat_measure("rmat-sssp", args.scale, 3)}
 
     cpu = None
     certified = None
@@ -485,6 +500,8 @@ def run_ours(args):
         line["certified_vs_oracle"] = certified
         if single is not None:
             line["one_source_per_launch"] = single
+        if others is not None:
+            line["other_configs"] = others
         if batch4 is not None:
             line["batch_1024"] = {k: batch4[k] for k in (
                 "value", "unit", "one_at_a_time", "exact_batched_eq_alone_eq_oracle",
@@ -756,28 +773,25 @@ def batch_measure(args, with_cpu: bool = True) -> dict:
     return line
 
 
-def run_serve(args):
-    """Served A*/PPSP on the road-like 4900 x 4900 grid: a seeded Poisson stream of
-    queries (kind by coin, targets log-uniform 10..1000 grid steps away) admitted into a
-    continuous-batching server as slots free up; latency = completion - arrival.  The same
-    arrivals served one query per launch give the baseline."""
-    import torch
-    import graphgen
+def serve_measure(g, G, total: int, rates, slots: int, budget_us: int, fusion: int,
+                  sequential: int) -> dict:
+    """Served A*/PPSP on graph g: a seeded Poisson stream of ``total`` queries (kind by
+    coin, targets log-uniform 10..1000 grid steps away) admitted into a continuous-
+    batching server as slots free up, at each offered rate; latency = completion -
+    arrival.  The first ``sequential`` arrivals of the first rate served one query per
+    launch give the baseline; served == alone for all of them and == the oracle on a
+    sample (outside every timed loop)."""
     import paper_1911_07260_gb300 as og
-    torch.cuda.init()
-    g = graphgen.road(args.side, 0.15, 0.02, seed=1)
-    G = og.Graph.from_csr(g)
-    total = args.queries
-    pairs = graphgen.sample_pairs_grid_steps(g, total, 10, 1000, seed=2, log_uniform=True)
+    pairs = graphgen_pairs(g, total)
     rng = np.random.default_rng(7)
     kinds = np.where(rng.random(total) < 0.5, og.Q_ASTAR, og.Q_PPSP)
     tune = og.autotune(G, og.Q_PPSP, pairs[:32, 0], pairs[:32, 1], 1 << 6, 1 << 14)
-    cfg = og.config(delta=int(tune.delta), fusion_threshold=args.serve_fusion)
+    cfg = og.config(delta=int(tune.delta), fusion_threshold=fusion)
     results = {}
     lines = []
-    for rate in args.rates:
+    for rate in rates:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
-        srv = og.Server(G, max_slots=args.slots, cfg=cfg)
+        srv = og.Server(G, max_slots=slots, cfg=cfg)
         lat = np.zeros(total)
         got = np.zeros(total, np.uint32)
         nxt = done = 0
@@ -789,7 +803,7 @@ def run_serve(args):
                 if not srv.submit(int(kinds[nxt]), int(pairs[nxt, 0]), int(pairs[nxt, 1]), nxt):
                     break
                 nxt += 1
-            active = srv.step(budget_us=args.budget_us)
+            active = srv.step(budget_us=budget_us)
             steps += 1
             tags, d = srv.poll()
             if len(tags):
@@ -807,9 +821,9 @@ def run_serve(args):
                       "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                       "steps": steps})
     # one query per launch, same arrivals (first rate), FIFO order
-    rate = args.rates[0]
+    rate = rates[0]
     arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, total))
-    nseq = min(total, args.sequential)
+    nseq = min(total, sequential)
     lat_s = np.zeros(nseq)
     seq = np.zeros(nseq, np.uint32)
     t0 = time.perf_counter()
@@ -829,7 +843,89 @@ def run_serve(args):
     ref = [oracle.ppsp(g, int(pairs[i, 0]), int(pairs[i, 1])) for i in sample]
     cpu_s = time.perf_counter() - t0
     exact &= all(int(seq[i]) == r for i, r in zip(sample, ref))
-    best = max(lines, key=lambda x: x["queries_per_s"])
+    return {"delta": int(cfg.delta), "served": lines,
+            "one_at_a_time": {"rate_per_s": rate, "queries": nseq,
+                              "queries_per_s": round(nseq / seq_wall, 1),
+                              "p50_ms": round(float(np.percentile(lat_s, 50)) * 1e3, 3),
+                              "p99_ms": round(float(np.percentile(lat_s, 99)) * 1e3, 3)},
+            "exact_served_eq_alone_eq_oracle": exact,
+            "cpu_baseline": {"value": round(len(sample) / cpu_s, 2), "unit": "queries/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sample)} of the queries, Dijkstra stopped at "
+                                       "the target"}}
+
+
+def rmat_measure(wl: str, scale: int, steps: int) -> dict:
+    """The R-MAT configuration in brief: the graph and 8 sources of ``--workload wl``, one
+    launch of all 8 per step with the schedule that workload's tuner picks (wBFS: the
+    defaults; SSSP: Delta 256, fusion off, tile 256, hub degree 1024), device time of
+    ``steps`` steps after two warm-ups; two sources' distances certified by the oracle's
+    certificate outside the timed loop."""
+    import torch
+    import graphgen
+    import oracle
+    import paper_1911_07260_gb300 as og
+    whi = 24 if wl == "rmat-wbfs" else 1 << 16
+    g = graphgen.rmat(scale, 16, 0.57, 0.19, 0.19, 1, whi, seed=1)
+    G = og.Graph.from_csr(g)
+    srcs = graphgen.sample_sources(g, 8, seed=2)
+    kind = og.Q_WBFS if wl == "rmat-wbfs" else og.Q_SSSP
+    cfg = None if kind == og.Q_WBFS else og.config(
+        delta=256, fusion_threshold=og.FUSION_OFF, expand_tile=256, hub_degree=1024)
+    queries = [(kind, int(s), 0, 0) for s in srcs]
+    dbuf = torch.empty(len(queries) * g.n, dtype=torch.int32, device="cuda")
+    og.batch_run(G, queries, cfg=cfg, out=dbuf)
+    dh = dbuf.cpu().numpy().view(np.uint32).reshape(len(queries), g.n)
+    m_r = sum(reached_edges(g, dh[i])[0] for i in range(len(queries)))
+    og.batch_run(G, queries, cfg=cfg, out=dbuf)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernel_ns = 0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        _, _, st = og.batch_run(G, queries, cfg=cfg, out=dbuf)
+        kernel_ns += st.kernel_ns
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) / 1e3 / steps
+    same = bool(np.array_equal(dbuf.cpu().numpy().view(np.uint32).reshape(len(queries), g.n),
+                               dh))
+    certified = same and all(oracle.check_sssp(g, int(srcs[i]), dh[i]) == (0, 0)
+                             for i in range(2))
+    order, moved = G.order()
+    out = {"workload": f"R-MAT scale {scale}: 8 {'wBFS' if kind == og.Q_WBFS else 'SSSP'} "
+                       "sources per launch",
+           "value": round(m_r / step_s / 1e9, 4), "unit": "GTEPS",
+           "ms_per_step": round(step_s * 1e3, 3),
+           "kernel_ms": round(kernel_ns / 1e6 / steps, 3), "steps": steps,
+           "vertex_order": "hot-first" if order == og.ORDER_HOT_FIRST else "as given",
+           "moved_vertices": moved,
+           "certified_vs_oracle": certified,
+           "steps_identical": same}
+    G.free()
+    del dbuf
+    torch.cuda.empty_cache()
+    return out
+
+
+def graphgen_pairs(g, total: int):
+    import graphgen
+    return graphgen.sample_pairs_grid_steps(g, total, 10, 1000, seed=2, log_uniform=True)
+
+
+def run_serve(args):
+    """Served A*/PPSP on the road-like 4900 x 4900 grid (serve_measure), one line."""
+    import torch
+    import graphgen
+    import paper_1911_07260_gb300 as og
+    torch.cuda.init()
+    g = graphgen.road(args.side, 0.15, 0.02, seed=1)
+    G = og.Graph.from_csr(g)
+    total = args.queries
+    r = serve_measure(g, G, total, args.rates, args.slots, args.budget_us, args.serve_fusion,
+                      args.sequential)
+    best = max(r["served"], key=lambda x: x["queries_per_s"])
     line = {
         "metric": "served A*/PPSP queries/s with p50/p99 latency",
         "value": best["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": total,
@@ -838,17 +934,12 @@ def run_serve(args):
         "data": "synthetic",
         "config": {"workload": f"road-like {args.side}x{args.side} grid, {total} Poisson "
                                "A*/PPSP queries, continuous batching",
-                   "slots": args.slots, "delta": int(cfg.delta), "budget_us": args.budget_us,
+                   "slots": args.slots, "delta": r["delta"], "budget_us": args.budget_us,
                    "fusion_threshold": args.serve_fusion},
-        "served": lines,
-        "one_at_a_time": {"rate_per_s": rate, "queries": nseq,
-                          "queries_per_s": round(nseq / seq_wall, 1),
-                          "p50_ms": round(float(np.percentile(lat_s, 50)) * 1e3, 3),
-                          "p99_ms": round(float(np.percentile(lat_s, 99)) * 1e3, 3)},
-        "exact_served_eq_alone_eq_oracle": exact,
-        "cpu_baseline": {"value": round(len(sample) / cpu_s, 2), "unit": "queries/s",
-                         "cores": 1, "kind": "oracle",
-                         "sample": f"{len(sample)} of the queries, Dijkstra stopped at the target"},
+        "served": r["served"],
+        "one_at_a_time": r["one_at_a_time"],
+        "exact_served_eq_alone_eq_oracle": r["exact_served_eq_alone_eq_oracle"],
+        "cpu_baseline": r["cpu_baseline"],
     }
     print(json.dumps(line), flush=True)
 
