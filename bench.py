@@ -84,6 +84,8 @@ def parse_args(argv=None):
     p.add_argument("--pull-divisor", type=int, default=0,
                    help="direction optimisation: pull a query's round when its frontier "
                         "exceeds n / this (0 = always push)")
+    p.add_argument("--order", choices=["auto", "hot", "user"], default="auto",
+                   help="device vertex order of the searched graph (default: the upload's)")
     p.add_argument("--no-configs", action="store_true",
                    help="road-sssp: skip the brief serve and R-MAT runs")
     p.add_argument("--no-batch", action="store_true",
@@ -284,6 +286,8 @@ def run_ours(args):
 
     g, gname, srcs = build_workload(args, rank, world)
     G = og.Graph.from_csr(g)
+    if args.order != "auto":
+        G.set_order({"hot": og.ORDER_HOT_FIRST, "user": og.ORDER_USER}[args.order])
     kind = {"rmat-wbfs": og.Q_WBFS, "road-bf": og.Q_BF}.get(args.workload, og.Q_SSSP)
     cfg = None
     # eager-vs-lazy comparison (Section 6.4): both with the schedule that suits the graph
@@ -487,6 +491,8 @@ def run_ours(args):
                        "pull_divisor": int(eff.pull_divisor),
                        "prefetch": int(eff.prefetch) == 1,
                        "bucket_update": "lazy" if int(eff.bucket_update) == 2 else "eager",
+                       "vertex_order": "hot-first" if G.order()[0] == og.ORDER_HOT_FIRST
+                                       else "as given",
                        "l2": "inputs larger than L2 (graph %.0f MB + dist %.0f MB > 129 MB)"
                              % ((8 * g.m + 4 * g.n) / 1e6, 4 * nq * g.n / 1e6),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
