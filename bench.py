@@ -963,12 +963,12 @@ def run_kcore(args):
     torch.cuda.init()
     g = graphgen.rmat(args.scale, 16, 0.57, 0.19, 0.19, 1, 2, seed=1)
     G = og.Graph.from_csr(g)
-    G.set_config(og.config(hub_degree=args.hub, expand_tile=args.tile))
+    kcfg = og.config(hub_degree=args.hub, expand_tile=args.tile)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
-    core, st0 = og.kcore(G, og.KCORE_LAZY, out=out)
+    core, st0 = og.kcore(G, og.KCORE_LAZY, cfg=kcfg, out=out)
     ref_core = out.cpu().numpy().view(np.uint32).copy()
     for _ in range(args.warmup):
-        og.kcore(G, og.KCORE_LAZY, out=out)
+        og.kcore(G, og.KCORE_LAZY, cfg=kcfg, out=out)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -977,7 +977,7 @@ def run_kcore(args):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            _, st = og.kcore(G, og.KCORE_LAZY, out=out)
+            _, st = og.kcore(G, og.KCORE_LAZY, cfg=kcfg, out=out)
             kernel_ns += st.kernel_ns
         e1.record(stream)
         torch.cuda.synchronize()
@@ -987,7 +987,7 @@ def run_kcore(args):
     same = True
     best_e = None
     for _ in range(max(2, args.steps // 5)):
-        _, se = og.kcore(G, og.KCORE_EAGER, out=out)
+        _, se = og.kcore(G, og.KCORE_EAGER, cfg=kcfg, out=out)
         same &= bool(np.array_equal(out.cpu().numpy().view(np.uint32), ref_core))
         if best_e is None or se.kernel_ns < best_e.kernel_ns:
             best_e = se
@@ -995,7 +995,7 @@ def run_kcore(args):
     t0 = time.perf_counter()
     reps = max(2, args.steps // 4)
     for _ in range(reps):
-        og.kcore(G, og.KCORE_LAZY, out=host)
+        og.kcore(G, og.KCORE_LAZY, cfg=kcfg, out=host)
     e2e_s = (time.perf_counter() - t0) / reps
     same &= bool(np.array_equal(host, ref_core))
     # bytes: per edge the neighbour id, its priority and its counter (4 + 4 + 4); per
@@ -1026,8 +1026,8 @@ def run_kcore(args):
         "config": {"workload": f"R-MAT scale {args.scale} k-core (coreness of every vertex), "
                                "one persistent launch per step", "n": g.n, "m": g.m,
                    "max_coreness": int(ref_core.max()),
-                   "hub_degree": int(G.get_config().hub_degree),
-                   "expand_tile": int(G.get_config().expand_tile),
+                   "hub_degree": args.hub or 256,
+                   "expand_tile": args.tile or int(G.get_config().expand_tile),
                    "l2": "inputs larger than L2 (graph %.0f MB)" % (8 * g.m / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / kernel_s / 1e9, 1),
                      "peak": peak, "unit": "GB/s",

@@ -220,7 +220,7 @@ constexpr uint32_t kHubSlots = 65536;       // hubs listed per round
 constexpr uint32_t kHubChunks = 1u << 20;   // 1024-edge hub chunks per round
 constexpr uint32_t kKcoreHub = 256;         // k-core: default hub out-degree
 constexpr uint32_t kSetcoverHub = 32;       // set cover: residual size of a large set
-constexpr int kSetcoverBps = 2;             // set cover: default CTAs per SM
+constexpr int kSetcoverBps = 4;             // set cover: default CTAs per SM
 constexpr int kKcoreBps = 2;                // k-core: default CTAs per SM
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 // Hot-first packing: the n / kHotDiv vertices of largest degree move to ids [0, n / kHotDiv),
@@ -1290,12 +1290,11 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* ucfg, uint32_t* core_o
   P.ks = ws.kstate.as<KState>();
   P.stats = ws.stats.as<Stats>();
   // Hubs (out-degree >= hub_degree) are split over every warp after the round's peel.
-  // Unset, the threshold is lower than for Delta-stepping: a peeling round has one
+  // Unset by the caller, the threshold is lower than for Delta-stepping, and the graph's
+  // stored schedule (tuned for Delta-stepping) is not used: a peeling round has one
   // frontier and no fused levels, so moving its long adjacency lists to the balanced hub
-  // pass costs little (R-MAT-24, lazy: 100 ms at 4096, 82 ms at 256).
-  const uint32_t hub_min = (ucfg && ucfg->hub_degree) ? ucfg->hub_degree
-                           : g->cfg.hub_degree        ? g->cfg.hub_degree
-                                                      : kKcoreHub;
+  // pass costs little (R-MAT-24, lazy: 60.2 ms at 4096, 49.4 ms at 256).
+  const uint32_t hub_min = (ucfg && ucfg->hub_degree) ? ucfg->hub_degree : kKcoreHub;
   const uint32_t hub_cap = g->max_deg >= hub_min ? kHubSlots : 0u;
   if (hub_cap) {
     TRY(ws.big.ensure(sizeof(BigItem) * hub_cap));
@@ -1366,6 +1365,9 @@ int og_setcover(og_graph* g, uint32_t eps_ppm, const uint32_t* priority, const o
   int occ = 0;
   CK(setcover_occupancy(&occ));
   if (occ < 1) return OG_E_CUDA;
+  // CTAs per SM: the caller's, else 4 -- a step's phases are short, and more resident
+  // warps hide more of their dependent gathers (R-MAT-24: 106.1 ms at 1, 82.5 ms at 2,
+  // 75.0 ms at 4).
   const int want = (ucfg && ucfg->blocks_per_sm) ? (int)ucfg->blocks_per_sm : kSetcoverBps;
   const int bps = std::max(1, std::min(want, occ));
   // The bucket ladder t_0 = 1, t_(j+1) = t_j + max(1, floor(t_j * eps)) until it passes
