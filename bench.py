@@ -76,7 +76,9 @@ def parse_args(argv=None):
     p.add_argument("--queries", type=int, default=20000, help="serve: queries in the stream")
     p.add_argument("--rates", type=float, nargs="+", default=[10000.0],
                    help="serve: Poisson arrival rates (queries/s)")
-    p.add_argument("--slots", type=int, default=128, help="serve: resident query slots")
+    p.add_argument("--slots", type=int, default=128,
+                   help="serve: resident query slots (0: as many as device memory allows, "
+                        "at most 512 -- the library's own sizing)")
     p.add_argument("--budget-us", type=int, default=400, help="serve: time per launch")
     p.add_argument("--serve-fusion", type=int, default=64, help="serve: fusion threshold")
     p.add_argument("--sequential", type=int, default=2000,
@@ -449,7 +451,9 @@ def run_ours(args):
                               args.serve_fusion, 300)
         others = {"serve": {"workload": f"{gname}, 5000 Poisson A*/PPSP queries offered at "
                                         "20,000/s (saturating), continuous batching, "
-                                        f"{args.slots} slots",
+                                        f"{serve['slots']} slots"
+                                        + (" (sized by device memory)" if not args.slots
+                                           else ""),
                             **{k: serve[k] for k in ("served", "one_at_a_time",
                                                      "exact_served_eq_alone_eq_oracle")}},
                   "rmat_wbfs": rmat_measure("rmat-wbfs", args.scale, 3),
@@ -798,6 +802,7 @@ def serve_measure(g, G, total: int, rates, slots: int, budget_us: int, fusion: i
     for rate in rates:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
         srv = og.Server(G, max_slots=slots, cfg=cfg)
+        resident = srv.max_slots
         lat = np.zeros(total)
         got = np.zeros(total, np.uint32)
         nxt = done = 0
@@ -849,7 +854,7 @@ def serve_measure(g, G, total: int, rates, slots: int, budget_us: int, fusion: i
     ref = [oracle.ppsp(g, int(pairs[i, 0]), int(pairs[i, 1])) for i in sample]
     cpu_s = time.perf_counter() - t0
     exact &= all(int(seq[i]) == r for i, r in zip(sample, ref))
-    return {"delta": int(cfg.delta), "served": lines,
+    return {"delta": int(cfg.delta), "slots": resident, "served": lines,
             "one_at_a_time": {"rate_per_s": rate, "queries": nseq,
                               "queries_per_s": round(nseq / seq_wall, 1),
                               "p50_ms": round(float(np.percentile(lat_s, 50)) * 1e3, 3),
@@ -940,7 +945,7 @@ def run_serve(args):
         "data": "synthetic",
         "config": {"workload": f"road-like {args.side}x{args.side} grid, {total} Poisson "
                                "A*/PPSP queries, continuous batching",
-                   "slots": args.slots, "delta": r["delta"], "budget_us": args.budget_us,
+                   "slots": r["slots"], "delta": r["delta"], "budget_us": args.budget_us,
                    "fusion_threshold": args.serve_fusion},
         "served": r["served"],
         "one_at_a_time": r["one_at_a_time"],
