@@ -559,48 +559,62 @@ __device__ void redist_task(const AParams& P, uint32_t q, uint32_t mode, uint32_
   settle(P, q, 0u - k);
 }
 
-// Claims up to 32 entries of some query's current task.  Lane 0 searches, starting at
-// query `rot`; the claim is broadcast to the warp.
+// Claims up to 32 entries of some query's current task.  The warp looks at 32 queries at
+// a time, starting at query `rot` (lane i at rot + i): every lane reads its query's claim
+// word, and those that are open also read the task's limit, so a round of the search
+// costs three round trips however many of the 32 queries are finished or idle.  The open
+// queries with entries left are then tried in lane order by compare-and-swap on their
+// claim words (a lane that loses its compare-and-swap reads its query again; eight
+// attempts per group of 32); the claim is broadcast to the warp.
 __device__ bool claim(const AParams& P, uint32_t& rot, uint32_t& q, uint32_t& mode,
                       uint32_t& cur, uint32_t& start, uint32_t& k) {
   const uint32_t lane = threadIdx.x & 31;
-  uint32_t got = 0, tq = 0, tm = 0, tc = 0, ts = 0, tk = 0;
-  if (lane == 0) {
-    for (uint32_t a = 0; a < P.nq && !got; ++a) {
-      const uint32_t qq = (rot + a) % P.nq;
-      AQState* s = P.aq + qq;
-      for (int tries = 0; tries < 8; ++tries) {
-        const unsigned long long w = ld_acquire64(&s->word);
-        const uint32_t c = (uint32_t)w;
-        if (c == kClosed) break;
-        const uint32_t m = __ldcg(&s->mode);
-        const uint32_t cu = __ldcg(&s->cur);
-        const uint32_t lim = m == kMRelax
-                                 ? min(__ldcg(P.counts + (size_t)qq * P.B + (cu & P.Bmask)), P.cap)
-                                 : __ldcg(&s->limit);
-        if (c >= lim) break;
-        const uint32_t kk = min(32u, lim - c);
-        if (atomicCAS(&s->word, w, w + kk) == w) {
-          got = 1;
-          tq = qq;
-          tm = m;
-          tc = cu;
-          ts = c;
-          tk = kk;
-          break;
+  for (uint32_t a0 = 0; a0 < P.nq; a0 += 32) {
+    const uint32_t qq = (rot + a0 + lane) % P.nq;
+    AQState* s = P.aq + qq;
+    unsigned long long w = 0ull;
+    uint32_t c = 0, m = 0, cu = 0, lim = 0;
+    if (a0 + lane < P.nq) {
+      w = ld_acquire64(&s->word);
+      c = (uint32_t)w;
+      if (c != kClosed) {
+        m = __ldcg(&s->mode);
+        cu = __ldcg(&s->cur);
+        lim = m == kMRelax ? min(__ldcg(P.counts + (size_t)qq * P.B + (cu & P.Bmask)), P.cap)
+                           : __ldcg(&s->limit);
+      }
+    }
+    for (int tries = 0; tries < 8; ++tries) {
+      const unsigned open = __ballot_sync(FULL, a0 + lane < P.nq && c != kClosed && c < lim);
+      if (!open) break;
+      const int l = __ffs(open) - 1;
+      uint32_t got = 0;
+      if ((int)lane == l) {
+        got = atomicCAS(&s->word, w, w + min(32u, lim - c)) == w ? 1u : 0u;
+        if (!got) {  // another warp moved the word first: look at the query again
+          w = ld_acquire64(&s->word);
+          c = (uint32_t)w;
+          if (c != kClosed) {
+            m = __ldcg(&s->mode);
+            cu = __ldcg(&s->cur);
+            lim = m == kMRelax
+                      ? min(__ldcg(P.counts + (size_t)qq * P.B + (cu & P.Bmask)), P.cap)
+                      : __ldcg(&s->limit);
+          }
         }
+      }
+      if (__shfl_sync(FULL, got, l)) {
+        q = __shfl_sync(FULL, qq, l);
+        mode = __shfl_sync(FULL, m, l);
+        cur = __shfl_sync(FULL, cu, l);
+        start = __shfl_sync(FULL, c, l);
+        k = __shfl_sync(FULL, min(32u, lim - c), l);
+        rot = q;
+        return true;
       }
     }
   }
-  got = __shfl_sync(FULL, got, 0);
-  if (!got) return false;
-  q = __shfl_sync(FULL, tq, 0);
-  mode = __shfl_sync(FULL, tm, 0);
-  cur = __shfl_sync(FULL, tc, 0);
-  start = __shfl_sync(FULL, ts, 0);
-  k = __shfl_sync(FULL, tk, 0);
-  rot = q;
-  return true;
+  return false;
 }
 
 template <bool ELL>
