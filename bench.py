@@ -491,7 +491,7 @@ def run_ours(args):
                        "hub_degree": int(eff.hub_degree),
                        "blocks_per_sm": int(eff.blocks_per_sm),
                        "engine": "async" if int(eff.engine) == 2 else "rounds",
-                       "layout": "ell" if int(eff.layout) == 2 else "csr",
+                       "layout": "ell" if ell_rows else "csr",  # the path that ran
                        "pull_divisor": int(eff.pull_divisor),
                        "prefetch": int(eff.prefetch) == 1,
                        "bucket_update": "lazy" if int(eff.bucket_update) == 2 else "eager",
