@@ -95,6 +95,17 @@ def test_null_arguments_are_rejected_before_any_device_call(og):
     assert L.og_setcover(fake, 1000001, None, None, out, None, None) == og.E_INVALID
     assert L.og_setcover(fake, 10000, None, None, None, None, None) == og.E_INVALID
     assert L.og_kcore(fake, 7, None, out, None, None) == og.E_INVALID
+    # vertex order: NULL graph, unknown order
+    assert L.og_graph_set_order(None, og.ORDER_HOT_FIRST, None) == og.E_INVALID
+    assert L.og_graph_set_order(fake, 3, None) == og.E_INVALID
+    assert L.og_graph_get_order(None, None, None) == og.E_INVALID
+    # probe: chain counts other than 1, 2, 4, 8, 16, threads not a multiple of 32, sizes
+    # that are not powers of two, a footprint larger than the array
+    ns = ctypes.c_double()
+    for args in ((0, 1 << 20, 1 << 20, 4, 256, 3, 10), (0, 1 << 20, 1 << 20, 4, 256, 32, 10),
+                 (0, 1 << 20, 1 << 20, 4, 100, 1, 10), (0, 3 << 20, 1 << 20, 4, 256, 1, 10),
+                 (0, 1 << 20, 1 << 21, 4, 256, 1, 10), (3, 1 << 20, 1 << 20, 4, 256, 1, 10)):
+        assert L.og_probe_chain(*args, ctypes.byref(ns)) == og.E_INVALID, args
 
 
 def test_launch_status_mapping_on_hand_built_error_words(og):
