@@ -201,6 +201,12 @@ def clock_summary(lines) -> dict:
 # reports null.
 TRAFFIC_CAPTURE = {"kernel_sha": "a5391d8bfc90b34d", "bytes": 2.5669e9, "n": 5756935,
                    "sources": 8, "kind": "road"}
+# DRAM bytes of one full-size R-MAT-24 launch (8 sources, hot-first order) from a one-pass
+# capture of that very launch (profiles/og_delta_kernel_rmat24_traffic.md), keyed like
+# the road capture and by the schedule (Delta, fusion threshold, tile, hub degree) it ran.
+RMAT_TRAFFIC = {"kernel_sha": "a5391d8bfc90b34d", "scale": 24, "sources": 8,
+                "rmat-sssp": {"bytes": 141472959744, "schedule": (256, 0xFFFFFFFE, 256, 1024)},
+                "rmat-wbfs": {"bytes": 85332831488, "schedule": None}}
 KERNEL_SOURCES = ["paper_1911_07260_gb300/csrc/og_kernels.cu",
                   "paper_1911_07260_gb300/csrc/og_device.cuh",
                   "paper_1911_07260_gb300/csrc/og_internal.cuh"]
@@ -219,6 +225,18 @@ def kernel_sha() -> str:
         src = re.sub(r"//[^\n]*", "", src)
         h.update("\n".join(l.rstrip() for l in src.split("\n") if l.strip()).encode())
     return h.hexdigest()[:16]
+
+
+def rmat_traffic(workload: str, scale: int, sources: int, hot_first: bool, schedule):
+    """The captured full-size R-MAT traffic when this run is that launch, else None."""
+    c = RMAT_TRAFFIC
+    e = c.get(workload)
+    if (e is None or scale != c["scale"] or sources != c["sources"] or not hot_first
+            or kernel_sha() != c["kernel_sha"]):
+        return None
+    if e["schedule"] is not None and tuple(e["schedule"]) != tuple(schedule):
+        return None
+    return e["bytes"]
 
 
 def scaled_traffic(kind: str, n: int, sources: int, engine: int):
@@ -375,8 +393,17 @@ def run_ours(args):
     ell_rows = int(np.diff(g.offsets).max(initial=0)) <= 8 and int(eff.layout) in (0, 2) \
         and int(eff.bucket_update) != 2
     kname = "og_delta_ell_kernel" if ell_rows else "og_delta_kernel"
-    traffic = scaled_traffic({"road-sssp": "road", "road-bf": "bf"}.get(args.workload, "rmat"),
-                             g.n, nq, int(eff.engine)) if ell_rows else None
+    if ell_rows:
+        traffic = scaled_traffic({"road-sssp": "road", "road-bf": "bf"}.get(args.workload, "rmat"),
+                                 g.n, nq, int(eff.engine))
+    else:
+        resolved = G.get_config() if cfg is None else cfg
+        sched = (int(resolved.delta), int(resolved.fusion_threshold), int(resolved.expand_tile),
+                 int(resolved.hub_degree))
+        traffic = rmat_traffic(args.workload, args.scale, nq,
+                               G.order()[0] == og.ORDER_HOT_FIRST, sched) \
+            if int(eff.engine) != 2 and int(eff.bucket_update) != 2 and not args.pull_divisor \
+            else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind, "kernel": kname,

@@ -38,6 +38,24 @@ def test_scaled_traffic_follows_vertices_times_sources(monkeypatch):
     assert bench.scaled_traffic("road", cap["n"], cap["sources"], 1) is None
 
 
+def test_rmat_traffic_only_for_the_captured_launch(monkeypatch):
+    """The full-size R-MAT capture is reported only for the launch it measured: the same
+    workload, scale, sources, hot-first order, schedule and kernel code."""
+    cap = bench.RMAT_TRAFFIC
+    monkeypatch.setattr(bench, "kernel_sha", lambda: cap["kernel_sha"])
+    sched = cap["rmat-sssp"]["schedule"]
+    assert bench.rmat_traffic("rmat-sssp", 24, 8, True, sched) == cap["rmat-sssp"]["bytes"]
+    assert bench.rmat_traffic("rmat-wbfs", 24, 8, True, (1, 1024, 256, 4096)) == \
+        cap["rmat-wbfs"]["bytes"]
+    assert bench.rmat_traffic("rmat-sssp", 24, 8, True, (128,) + tuple(sched[1:])) is None
+    assert bench.rmat_traffic("rmat-sssp", 22, 8, True, sched) is None
+    assert bench.rmat_traffic("rmat-sssp", 24, 2, True, sched) is None
+    assert bench.rmat_traffic("rmat-sssp", 24, 8, False, sched) is None
+    assert bench.rmat_traffic("road-sssp", 24, 8, True, sched) is None
+    monkeypatch.setattr(bench, "kernel_sha", lambda: "0" * 16)
+    assert bench.rmat_traffic("rmat-sssp", 24, 8, True, sched) is None
+
+
 def test_kernel_sha_covers_the_kernel_sources():
     sha = bench.kernel_sha()
     assert len(sha) == 16 and int(sha, 16) >= 0
