@@ -199,7 +199,10 @@ def clock_summary(lines) -> dict:
 # launch is too large for a multi-pass capture), scaled by vertices x sources to the
 # benchmarked graph.  It describes the kernel sources it was taken on; any other build
 # reports null.
-TRAFFIC_CAPTURE = {"kernel_sha": "a5391d8bfc90b34d", "bytes": 2.5669e9, "n": 5756935,
+# DRAM bytes of one road-like 4900 x 4900 launch of 8 sources, from a one-pass capture of
+# that launch (profiles/og_delta_ell_kernel_road4900_traffic.md); other sizes are scaled
+# by vertices x sources.
+TRAFFIC_CAPTURE = {"kernel_sha": "a5391d8bfc90b34d", "bytes": 13.656772864e9, "n": 23997150,
                    "sources": 8, "kind": "road"}
 # DRAM bytes of one full-size R-MAT-24 launch (8 sources, hot-first order) from a one-pass
 # capture of that very launch (profiles/og_delta_kernel_rmat24_traffic.md), keyed like
