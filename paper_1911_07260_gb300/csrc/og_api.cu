@@ -1856,18 +1856,29 @@ int autotune_queries(og_graph* g, const std::vector<og_query>& qs, uint32_t delt
     c.prefetch = pf;
     consider(c);
   }
-  for (uint32_t t : {32u, 64u, 128u, 256u, 512u}) {
-    og_config c = best;
-    c.expand_tile = t;
-    consider(c);
-  }
-  if (g->max_deg >= 1024) {  // skewed degrees: where hubs go to the grid-wide pass
+  auto sweep_tile = [&]() {
+    for (uint32_t t : {32u, 64u, 128u, 256u, 512u}) {
+      og_config c = best;
+      c.expand_tile = t;
+      consider(c);
+    }
+  };
+  auto sweep_hub = [&]() {
+    if (g->max_deg < 1024) return;  // skewed degrees: where hubs go to the grid-wide pass
     for (uint32_t h : {1024u, 4096u, 32768u, 0xFFFFFFFFu}) {
       og_config c = best;
       c.hub_degree = h;
       consider(c);
     }
-  }
+  };
+  // The frontier tile and the hub threshold interact (hubs leave the tiles' edge lists),
+  // so they are swept twice: a tile picked under the default threshold can lose once the
+  // threshold moves (R-MAT-24 SSSP: tile 128 then hub 1024, 125.7 ms; tile 256 with hub
+  // 1024, 117.9 ms).
+  sweep_tile();
+  sweep_hub();
+  sweep_tile();
+  sweep_hub();
   for (uint32_t b = 1; b <= (uint32_t)std::max(1, g->occ); ++b) {
     og_config c = best;
     c.blocks_per_sm = b;
