@@ -209,7 +209,7 @@ TRAFFIC_CAPTURE = {"kernel_sha": "a5391d8bfc90b34d", "bytes": 13.656772864e9, "n
 # the road capture and by the schedule (Delta, fusion threshold, tile, hub degree) it ran.
 RMAT_TRAFFIC = {"kernel_sha": "a5391d8bfc90b34d", "scale": 24, "sources": 8,
                 "rmat-sssp": {"bytes": 141472959744, "schedule": (256, 0xFFFFFFFE, 256, 1024)},
-                "rmat-wbfs": {"bytes": 85332831488, "schedule": None}}
+                "rmat-wbfs": {"bytes": 85332831488, "schedule": (2, 1024, 256, 4096)}}
 KERNEL_SOURCES = ["paper_1911_07260_gb300/csrc/og_kernels.cu",
                   "paper_1911_07260_gb300/csrc/og_device.cuh",
                   "paper_1911_07260_gb300/csrc/og_internal.cuh"]
@@ -320,7 +320,9 @@ def run_ours(args):
     if eager_ref is not None:
         cfg = og.config(delta=eager_ref.delta, expand_tile=eager_ref.expand_tile,
                         hub_degree=eager_ref.hub_degree, bucket_update=og.UPDATE_LAZY)
-    elif not args.no_autotune and kind == og.Q_SSSP and not args.delta:
+    elif not args.no_autotune and kind in (og.Q_SSSP, og.Q_WBFS) and not args.delta:
+        # the library's tuner on the workload's own sources (wBFS: Delta is 1, the rest of
+        # the schedule is searched)
         lo, hi = (1 << 8, 1 << 16)
         cfg = og.autotune(G, kind, srcs, None, lo, hi)
     elif args.delta or args.fusion:

@@ -45,8 +45,9 @@ def test_rmat_traffic_only_for_the_captured_launch(monkeypatch):
     monkeypatch.setattr(bench, "kernel_sha", lambda: cap["kernel_sha"])
     sched = cap["rmat-sssp"]["schedule"]
     assert bench.rmat_traffic("rmat-sssp", 24, 8, True, sched) == cap["rmat-sssp"]["bytes"]
-    assert bench.rmat_traffic("rmat-wbfs", 24, 8, True, (1, 1024, 256, 4096)) == \
+    assert bench.rmat_traffic("rmat-wbfs", 24, 8, True, cap["rmat-wbfs"]["schedule"]) == \
         cap["rmat-wbfs"]["bytes"]
+    assert bench.rmat_traffic("rmat-wbfs", 24, 8, True, (2, 1024, 512, 4096)) is None
     assert bench.rmat_traffic("rmat-sssp", 24, 8, True, (128,) + tuple(sched[1:])) is None
     assert bench.rmat_traffic("rmat-sssp", 22, 8, True, sched) is None
     assert bench.rmat_traffic("rmat-sssp", 24, 2, True, sched) is None
