@@ -200,6 +200,12 @@ int og_graph_set_order(og_graph* g, uint32_t order, void* stream);
 /* The order in effect (OG_ORDER_HOT_FIRST or OG_ORDER_USER) and how many vertices have
  * a device id other than their own id (either pointer may be NULL). */
 int og_graph_get_order(const og_graph* g, uint32_t* order, uint32_t* moved);
+/* The hot-first order for out-degrees degrees[0 .. n) (host arrays; no device call):
+ * device_to_user[x] receives the caller's vertex stored at device id x, and *hot_edges
+ * (may be NULL) the edges the n/8 hottest vertices hold -- what og_graph_set_order
+ * applies and what the upload's rule weighs.  OG_E_INVALID for NULL arrays or n = 0. */
+int og_hot_first_order(const uint32_t* degrees, uint32_t n, uint32_t* device_to_user,
+                       uint64_t* hot_edges);
 
 /* n, m, minimum and maximum edge weight (any pointer may be NULL). */
 int og_graph_info(const og_graph* g, uint32_t* n, uint64_t* m, uint32_t* min_w,

@@ -87,6 +87,7 @@ def lib():
             "og_graph_set_coords": (i32, [vp, vp, vp]),
             "og_graph_set_order": (i32, [vp, u32, vp]),
             "og_graph_get_order": (i32, [vp, P(u32), P(u32)]),
+            "og_hot_first_order": (i32, [vp, u32, vp, P(u64)]),
             "og_graph_info": (i32, [vp, P(u32), P(u64), P(u32), P(u32)]),
             "og_graph_set_config": (i32, [vp, P(Config)]),
             "og_graph_get_config": (i32, [vp, P(Config)]),
@@ -402,6 +403,18 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+def hot_first_order(degrees):
+    """(device_to_user uint32[n], hot_edges): the hot-first order for these out-degrees,
+    computed on the host (``og_hot_first_order``)."""
+    deg = np.ascontiguousarray(degrees, dtype=np.uint32)
+    out = np.empty(deg.shape[0], np.uint32)
+    he = ctypes.c_uint64()
+    _check(lib().og_hot_first_order(deg.ctypes.data if deg.size else None, deg.shape[0],
+                                    out.ctypes.data if out.size else None, ctypes.byref(he)),
+           "og_hot_first_order")
+    return out, int(he.value)
 
 
 def autotune(g: Graph, kind: int, srcs, dsts=None, delta_lo: int = 0, delta_hi: int = 0) -> Config:

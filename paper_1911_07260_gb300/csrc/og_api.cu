@@ -1163,6 +1163,17 @@ int og_graph_set_order(og_graph* g, uint32_t order, void* stream) {
   return set_order(g, order, (cudaStream_t)stream);
 }
 
+int og_hot_first_order(const uint32_t* degrees, uint32_t n, uint32_t* device_to_user,
+                       uint64_t* hot_edges) {
+  if (!degrees || !device_to_user || n == 0) return OG_E_INVALID;
+  std::vector<uint32_t> deg(degrees, degrees + n), pi, dev;
+  uint64_t he = 0;
+  hot_first(deg, pi, dev, &he);
+  memcpy(device_to_user, pi.data(), sizeof(uint32_t) * n);
+  if (hot_edges) *hot_edges = he;
+  return OG_OK;
+}
+
 int og_graph_get_order(const og_graph* g, uint32_t* order, uint32_t* moved) {
   if (!g) return OG_E_INVALID;
   if (order) *order = g->h_pi.empty() ? OG_ORDER_USER : OG_ORDER_HOT_FIRST;
