@@ -779,11 +779,16 @@ def batch_measure(args, with_cpu: bool = True) -> dict:
             exact &= bool(np.array_equal(r, dist_b[i])) if kind == "sssp" else \
                 int(r) == int(d_batch[i])
     host = torch.empty(nq * g.n, dtype=torch.int32, pin_memory=True)
-    og.batch_run(G, queries, cfg=cfg, out=host.numpy())
+    hnp = host.numpy()
+    og.batch_run(G, queries, cfg=cfg, out=hnp)
+    reps = max(5, args.steps // 2)
+    laps = []
     t0 = time.perf_counter()
-    for _ in range(max(2, args.steps // 4)):
-        og.batch_run(G, queries, cfg=cfg, out=host.numpy())
-    e2e_s = (time.perf_counter() - t0) / max(2, args.steps // 4)
+    for _ in range(reps):
+        og.batch_run(G, queries, cfg=cfg, out=hnp)
+        laps.append(time.perf_counter())
+    e2e_s = (laps[-1] - t0) / reps  # the mean over the launches; the median beside it
+    e2e_med = float(np.median(np.diff([t0] + laps)))
     peak, peak_kind = peaks()
     line = {
         "metric": "batched queries/s (128 SSSP + 128 PPSP per launch)",
@@ -813,7 +818,8 @@ def batch_measure(args, with_cpu: bool = True) -> dict:
             "kind": "oracle", "sample": f"{len(sample)} of the queries (16 SSSP + 16 PPSP), "
                                         f"{threads} host threads, {cpu_s:.1f} s"},
         "e2e": {"value": round(nq / e2e_s, 2), "unit": "queries/s", "h2d_bytes_per_step": 16 * nq,
-                "d2h_bytes_per_step": 4 * nq * g.n},
+                "d2h_bytes_per_step": 4 * nq * g.n, "ms_per_step": round(e2e_s * 1e3, 3),
+                "median_ms_per_step": round(e2e_med * 1e3, 3), "steps": reps},
         "gpu_launches": 3 * args.steps,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
