@@ -252,7 +252,8 @@ int og_sssp_bellman_ford(og_graph* g, uint32_t src, uint32_t* dist_out, og_stats
  *   cfg: NULL or a config; used fields: expand_tile (frontier entries per claim, rounded
  *        up to 256; a small frontier gets smaller tiles), hub_degree (frontier vertices
  *        of at least this out-degree have their edges split over every warp of the grid;
- *        0 = 256 here), blocks_per_sm (0 = 2 here), spin_limit_ns,
+ *        0 = 256 here, whatever the graph's stored schedule), blocks_per_sm (0 = 2 here),
+ *        spin_limit_ns,
  *        arena_entries (vertex ids held by the
  *        256 materialised buckets; default 4n; a bucket that runs out of space is rebuilt
  *        by a scan at its level, so any size gives the same result).
@@ -288,7 +289,8 @@ int og_kcore(og_graph* g, uint32_t mode, const og_config* cfg, uint32_t* core_ou
  *        give the method's expected number of steps per bucket); NULL = the identity.
  *   cfg: NULL or a config; used fields: hub_degree (a set with at least this many
  *        uncovered elements has them split over every warp of the grid; 0 = 32; clamped
- *        to [16, 2^26]), blocks_per_sm (0 = 2), spin_limit_ns.
+ *        to [16, 2^26]), blocks_per_sm (0 = 4), spin_limit_ns.  The graph's stored
+ *        schedule (tuned for Delta-stepping) is not used.
  *   step_out: uint32[n], host or device: the 1-based step in which set v joined the
  *        cover, 0 if it did not.
  *   stats (may be NULL): rounds = steps, fused_iters = buckets worked off, items = set
