@@ -912,8 +912,8 @@ def serve_measure(g, G, total: int, rates, slots: int, budget_us: int, fusion: i
 
 def rmat_measure(wl: str, scale: int, steps: int) -> dict:
     """The R-MAT configuration in brief: the graph and 8 sources of ``--workload wl``, one
-    launch of all 8 per step with the schedule that workload's tuner picks (wBFS: the
-    defaults; SSSP: Delta 256, fusion off, tile 256, hub degree 1024), device time of
+    launch of all 8 per step with the schedule that workload's tuner picks (wBFS: fusion
+    off, tile 512; SSSP: Delta 256, fusion off, tile 256, hub degree 1024), device time of
     ``steps`` steps after two warm-ups; two sources' distances certified by the oracle's
     certificate outside the timed loop."""
     import torch
@@ -925,8 +925,9 @@ def rmat_measure(wl: str, scale: int, steps: int) -> dict:
     G = og.Graph.from_csr(g)
     srcs = graphgen.sample_sources(g, 8, seed=2)
     kind = og.Q_WBFS if wl == "rmat-wbfs" else og.Q_SSSP
-    cfg = None if kind == og.Q_WBFS else og.config(
-        delta=256, fusion_threshold=og.FUSION_OFF, expand_tile=256, hub_degree=1024)
+    cfg = og.config(fusion_threshold=og.FUSION_OFF, expand_tile=512) if kind == og.Q_WBFS \
+        else og.config(delta=256, fusion_threshold=og.FUSION_OFF, expand_tile=256,
+                       hub_degree=1024)
     queries = [(kind, int(s), 0, 0) for s in srcs]
     dbuf = torch.empty(len(queries) * g.n, dtype=torch.int32, device="cuda")
     og.batch_run(G, queries, cfg=cfg, out=dbuf)
