@@ -791,9 +791,14 @@ uint32_t user_id(const og_graph* g, uint32_t x) { return g->h_pi.empty() ? x : g
 int perm_rows(og_graph* g, Workspace& ws, uint32_t* rows, uint32_t nrows, bool to_user,
               cudaStream_t st) {
   if (g->nmv == 0 || nrows == 0) return OG_OK;
-  TRY(ws.permtmp.ensure(sizeof(uint32_t) * (size_t)g->nmv * nrows));
-  CK(launch_perm_rows(rows, g->n, nrows, g->mv, g->nmv, to_user, ws.permtmp.as<uint32_t>(),
-                      g->sms, st));
+  // Up to 16 rows at a time, so the staging of the moved entries stays small (the
+  // launches of one stream run in order, so the next group reuses it safely).
+  constexpr uint32_t kGroup = 16;
+  const uint32_t group = std::min(nrows, kGroup);
+  TRY(ws.permtmp.ensure(sizeof(uint32_t) * (size_t)g->nmv * group));
+  for (uint32_t r0 = 0; r0 < nrows; r0 += group)
+    CK(launch_perm_rows(rows + (size_t)r0 * g->n, g->n, std::min(group, nrows - r0), g->mv,
+                        g->nmv, to_user, ws.permtmp.as<uint32_t>(), g->sms, st));
   return OG_OK;
 }
 

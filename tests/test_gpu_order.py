@@ -70,6 +70,23 @@ def test_order_query_kinds_match_oracle(og, orc, gg):
             assert dres[-1] == orc.ppsp(g, srcs[0], srcs[1]), name
 
 
+def test_order_batch_of_many_rows(og, orc, gg):
+    """A batch of 40 queries (its rows go back to the caller's order 16 at a time), host
+    and device outputs, every row against the oracle."""
+    import torch
+    g = gg.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1000, seed=5)
+    G = _hot(og, g)
+    rng = np.random.default_rng(40)
+    srcs = [int(x) for x in rng.integers(0, g.n, 40)]
+    qs = [(og.Q_SSSP, s, 0, 64) for s in srcs]
+    ref = np.stack([orc.dijkstra(g, s) for s in srcs])
+    out, _, _ = og.batch_run(G, qs)
+    np.testing.assert_array_equal(out.reshape(len(qs), g.n), ref)
+    d = torch.empty(len(qs) * g.n, dtype=torch.int32, device="cuda")
+    og.batch_run(G, qs, out=d)
+    np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32).reshape(len(qs), g.n), ref)
+
+
 def test_order_astar_coordinates_stay_in_caller_order(og, orc, gg):
     """A* reads coordinates per vertex: set before or after the reorder, they stay
     attached to the caller's vertices."""
