@@ -12,6 +12,9 @@ Default workload (one line of JSON on rank 0):
           / device time per step (CUDA events on the launching stream)
   e2e     the same metric through og_batch_run with a pinned HOST distance buffer:
           the 8 x n distances come back over the host link inside the timed region
+  also    the same sources one per launch; the 256-query batch (config 4); and, outside
+          every timed loop of the main line, a brief served run and the R-MAT wBFS / SSSP
+          runs (other_configs), each checked against the oracle or its certificate
 The graph (760 MB) and the distance arrays (8 x 96 MB) exceed the 129 MB L2, so no L2
 flush is needed between steps.
 
@@ -22,7 +25,9 @@ ordered method's time on the same sources for the comparison of Section 6), rmat
 (coreness of R-MAT scale 24 by peeling, lazy with the histogram reduction and eager),
 road-lazy / rmat-lazy (SSSP with the lazy bucket update, the eager update's time on the
 same sources beside it: the eager-vs-lazy comparison of Section 6.4), rmat-setcover
-(approximate set cover of R-MAT scale 24, eps = 0.01, seeded random priorities).
+(approximate set cover of R-MAT scale 24, eps = 0.01, seeded random priorities),
+latency (the memory round-trip and random-access probes).  The R-MAT graphs are stored
+hot-first by the library (--order user keeps the caller's ids on the device).
 
 --impl reference times the CPU oracle (single-threaded Dijkstra) on the same workload
 and metric, one bounded sample per step.
