@@ -12,7 +12,9 @@
  * the paper's evaluation.  Every step runs in CUDA kernels for sm_103a; there is no CPU fallback.
  *
  * Conventions shared by every entry point
- *   - Vertices are uint32 ids in [0, n).  Weights are non-negative uint32.
+ *   - Vertices are uint32 ids in [0, n).  Weights are non-negative uint32.  Every id and
+ *     per-vertex array crossing this interface is in the caller's numbering, whatever
+ *     order the library keeps the graph in on the device (og_graph_set_order).
  *   - Distances are uint32; 0xFFFFFFFF means "unreachable" (the INT_MAX initialisation
  *     of the paper's priority vector, Section 4.1).  A path whose length reaches
  *     0xFFFFFFFE saturates there and the call returns OG_E_OVERFLOW.
