@@ -865,6 +865,7 @@ int set_order(og_graph* g, uint32_t order, cudaStream_t st) {
   const bool cur = !g->h_pi.empty();
   const bool pack = order != OG_ORDER_USER;
   if (pack == cur) return OG_OK;  // hot-first (of the same graph) or the user's already
+  if (order == OG_ORDER_AUTO && n < kHotMinN) return OG_OK;  // too small to pack
   std::vector<uint32_t> off(n + 1);
   CK(cudaMemcpyAsync(off.data(), g->off, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
